@@ -1,0 +1,150 @@
+/*
+ * jmg.h -- C ABI of the single-GPU dense SPD solver (sm_103a, GB300).
+ *
+ * The operations are those of the paper's `potrs` workflow ("Software design"
+ * section): solve A X = B for a symmetric positive-definite A through the
+ * Cholesky factorisation A = L L^T (potrf) followed by the two triangular
+ * solves (potrs); `posv` is both in one call.  The paper runs them through
+ * cuSOLVERMp on a 2D process grid; this library is a one-GPU implementation
+ * whose every step runs in its own CUDA kernels.
+ *
+ * Conventions (all entry points):
+ *  - Matrices are column-major: element (i, j) of A lives at A[i + j*lda].
+ *  - Only the LOWER triangle of A is read.  The strict upper triangle and the
+ *    padding rows n..lda-1 are never read or written.
+ *  - Every pointer to matrix data is a DEVICE pointer owned by the caller; the
+ *    library allocates no device memory.  Scratch space is the caller's `work`
+ *    buffer, sized by jmg_workspace_size() (alignment: 256 bytes).
+ *  - `stream` is a cudaStream_t passed as void*; work is queued on it in
+ *    order.  NULL means the legacy default stream.
+ *  - Return value: JMG_OK (0), -i when argument i (1-based) is illegal (LAPACK
+ *    style; nothing is queued), or a positive JMG_ERR_* code.
+ *  - `info` words are device pointers written asynchronously: 0, or k > 0 when
+ *    the leading minor of order k is not positive definite (its pivot is
+ *    <= 0 or NaN).  After a failure the factor is left partly computed, as in
+ *    LAPACK, and later kernels of the same call do nothing.
+ */
+#ifndef JMG_H
+#define JMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* storage type of A and B */
+typedef enum { JMG_F64 = 0, JMG_F32 = 1 } jmg_dtype;
+
+/* arithmetic of the trailing-matrix updates of the factorisation */
+typedef enum {
+  JMG_PREC_NATIVE = 0, /* FP64 throughout (potrf / potrs in place)              */
+  JMG_PREC_BF16 = 1,   /* BF16 tensor-core updates, FP32 accumulate, FP64 refine */
+  JMG_PREC_FP16 = 2,   /* FP16 tensor-core updates, FP32 accumulate, FP64 refine */
+  JMG_PREC_FP8 = 3     /* FP8 e4m3, power-of-two scale per 128x128 tile          */
+} jmg_prec;
+
+typedef enum { JMG_REFINE_IR = 0, JMG_REFINE_PCG = 1, JMG_REFINE_AUTO = 2 } jmg_refine;
+
+typedef enum { JMG_OP_POTRF = 0, JMG_OP_POTRS = 1, JMG_OP_POSV = 2 } jmg_op;
+
+enum {
+  JMG_OK = 0,
+  JMG_ERR_CUDA = 1,          /* a CUDA call or launch failed                       */
+  JMG_ERR_WORKSPACE = 2,     /* lwork smaller than jmg_workspace_size()            */
+  JMG_ERR_NOT_SPD = 3,       /* posv: the matrix is not positive definite          */
+  JMG_ERR_NOT_CONVERGED = 4, /* posv: refinement stopped above the tolerance       */
+  JMG_ERR_TIMEOUT = 5,       /* a device-side wait ran out; the kernel gave up     */
+  JMG_ERR_UNSUPPORTED = 6,   /* option combination not built                       */
+  JMG_ERR_ALIGN = 7          /* a pointer or leading dimension breaks alignment    */
+};
+
+/* Options; pass NULL for the defaults of jmg_default_options(). */
+typedef struct {
+  int nb;           /* diagonal-block / panel width (64 or 128)                     */
+  int NB;           /* depth of one trailing update (multiple of nb; 0 = nb)        */
+  int prec;         /* jmg_prec                                                     */
+  int words;        /* split words per tensor-core operand, 1..3 (BF16 / FP16)      */
+  double tol;       /* target normwise backward error of posv (mixed modes)         */
+  int maxit;        /* maximum refinement iterations                                */
+  int refine;       /* jmg_refine                                                   */
+  int shift_retry;  /* low-precision breakdown: retry with a diagonal shift (0/1)   */
+} jmg_options;
+
+/* Host-side report of one posv call (filled when the call returns). */
+typedef struct {
+  int status;       /* JMG_OK or JMG_ERR_*                                          */
+  int info;         /* potrf info of the (last) factorisation                       */
+  int iters;        /* refinement iterations performed                              */
+  int refine_used;  /* jmg_refine actually used (IR, or PCG after a switch)          */
+  int words_used;   /* split words of the factor                                    */
+  int factor_tries; /* 1 + number of shifted refactorisations                       */
+  double bwd_err;   /* final max_j ||b_j - A x_j||_inf / (||A||_inf ||x_j|| + ||b_j||) */
+  double shift;     /* diagonal shift of the factor (0 if none)                     */
+  double anorm;     /* ||A||_inf                                                     */
+  double t_factor_ms, t_solve_ms, t_refine_ms; /* host-timed phases (0 if not synced) */
+} jmg_stats;
+
+/* Fill *opt with the defaults: nb 128, NB 128, prec NATIVE, words 1, tol 1e-13,
+ * maxit 30, refine AUTO, shift_retry 1. */
+void jmg_default_options(jmg_options* opt);
+
+/* Bytes of `work` that the call (op, n, nrhs, dtype, opt) needs; 0 is valid. */
+size_t jmg_workspace_size(int op, int n, int nrhs, int dtype, const jmg_options* opt);
+
+/*
+ * potrf -- Cholesky factorisation A = L L^T in place (paper: "Software design",
+ * the factorisation step of potrs).
+ *   n       order of A (n >= 0; n == 0 is a no-op)
+ *   A       device, lower(A) in, lower(L) out; lda >= max(1, n)
+ *   dtype   JMG_F64 (JMG_F32 returns JMG_ERR_UNSUPPORTED)
+ *   info    device int, written asynchronously (see above); may not be NULL
+ *   opt     NULL or options (prec must be NATIVE)
+ *   work    may be NULL when jmg_workspace_size(JMG_OP_POTRF, ...) is 0
+ * Asynchronous: returns once the kernels are queued on `stream`.
+ */
+int jmg_potrf(int n, void* A, int lda, int dtype, int* info, const jmg_options* opt,
+              void* work, size_t lwork, void* stream);
+
+/*
+ * potrs -- solve (L L^T) X = B given the factor from jmg_potrf (paper:
+ * "Software design", the solve step of potrs): forward substitution
+ * L Y = B, then back substitution L^T X = Y.
+ *   L       device, lower(L) read; lda >= max(1, n)
+ *   B       device, n x nrhs, overwritten with X; ldb >= max(1, n)
+ * Asynchronous.
+ */
+int jmg_potrs(int n, int nrhs, const void* L, int lda, void* B, int ldb, int dtype,
+              void* work, size_t lwork, void* stream);
+
+/*
+ * posv -- solve A X = B (paper: "Software design", potrs as one call).
+ *   prec == NATIVE: potrf then potrs, in place (A becomes L), asynchronous.
+ *   prec != NATIVE: A is PRESERVED (it is needed for the FP64 residual).  The
+ *     factor is built in `work` with tensor-core trailing updates and used as
+ *     the preconditioner of an FP64 refinement loop that stops when the
+ *     backward error (see jmg_stats.bwd_err) is <= opt->tol.  This mode
+ *     synchronises `stream` once per refinement iteration and returns only when
+ *     X is final.  B is overwritten with X.
+ *   info    device int (potrf convention); may not be NULL
+ *   stats   host pointer or NULL
+ */
+int jmg_posv(int n, int nrhs, void* A, int lda, void* B, int ldb, int dtype, int* info,
+             const jmg_options* opt, jmg_stats* stats, void* work, size_t lwork,
+             void* stream);
+
+/*
+ * logdet -- log det A = 2 sum_i log L_ii from a factor made by jmg_potrf
+ * (paper: "Software design", potrs can also return log det A).
+ *   out     device double, written asynchronously
+ */
+int jmg_logdet(int n, const void* L, int lda, int dtype, double* out, void* stream);
+
+/* Human-readable name of a status code. */
+const char* jmg_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JMG_H */

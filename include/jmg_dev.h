@@ -1,0 +1,73 @@
+/*
+ * jmg_dev.h -- kernel-level entry points of the SPD solver library, exported
+ * for tests, benchmarks and profiling.  They run one building block of
+ * jmg_potrf / jmg_posv in isolation, on caller-owned device memory, queued on
+ * `stream` (a cudaStream_t passed as void*).  Conventions as in jmg.h.
+ */
+#ifndef JMG_DEV_H
+#define JMG_DEV_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * Trailing-matrix update on the tensor cores (the SYRK step of a right-looking
+ * blocked Cholesky factorisation):
+ *     C[i, j] -= sum_k PA[i, k] * PB[j, k]     for 0 <= j <= i < m
+ * PA, PB: m x kext, ROW-major (k contiguous), leading dimension ldp elements,
+ *   element type BF16 (prec JMG_PREC_BF16) or FP16 (JMG_PREC_FP16); kext and
+ *   ldp multiples of 64; base addresses 16-byte aligned.  PB may equal PA.
+ * C: FP32, column-major, ldc >= m; the strict upper triangle is not touched.
+ * err: device int; set non-zero if a device-side wait ran out (the update is
+ *   then incomplete).  Asynchronous.
+ */
+int jmg_dev_syrk_tc(int m, int kext, const void* PA, const void* PB, int ldp, int prec,
+                    float* C, int ldc, int* err, void* stream);
+
+/*
+ * FP8 (e4m3) variant with one power-of-two scale per 128 x 128 tile:
+ *     C[i, j] -= sum_c 2^-(e[i/128, c] + e[j/128, c]) * sum_{k in chunk c} Q[i, k] Q[j, k]
+ * Q: m x kext e4m3 bytes, row-major, ldq bytes (multiple of 128); e: int8
+ * exponents, row-major [ceil(m/128)] x [kext/128].  C as above.
+ */
+int jmg_dev_syrk_fp8(int m, int kext, const void* Q, int ldq, const signed char* e,
+                     float* C, int ldc, int* err, void* stream);
+
+/*
+ * FP64 residual R = B - A X with A symmetric (lower(A) read), the kernel that
+ * drives the refinement loop of jmg_posv.  X, B, R: n x nrhs column-major.
+ * Also writes colmax[0..nrhs) = ||r_j||_inf, colmax[nrhs..2nrhs) = ||x_j||_inf,
+ * colmax[2nrhs..3nrhs) = ||b_j||_inf.  work: jmg_dev_residual_workspace bytes.
+ */
+size_t jmg_dev_residual_workspace(int n, int nrhs);
+int jmg_dev_residual(int n, int nrhs, const double* A, int lda, const double* X, int ldx,
+                     const double* B, int ldb, double* R, int ldr, double* colmax,
+                     void* work, size_t lwork, void* stream);
+
+/* ||A||_inf of the symmetric matrix held in lower(A) (FP64), to *out. */
+int jmg_dev_norm_inf(int n, const double* A, int lda, double* out, void* work, size_t lwork,
+                     void* stream);
+
+/*
+ * Throughput probes: `blocks` CTAs of 256 threads each run `iters` rounds of
+ * independent dependent-chain arithmetic and store a checksum to sink[0..):
+ *   kind 0: FP64 fused multiply-add (DFMA), 2 flops each, 8 chains per thread
+ *   kind 1: FP64 mma.sync m8n8k4 (512 flops per warp instruction)
+ *   kind 2: FP32 fused multiply-add
+ * Returns the number of flops the launch performs in *flops.  The caller times
+ * the launch (CUDA events) to get a rate.
+ */
+int jmg_dev_probe(int kind, int blocks, int iters, double* sink, double* flops, void* stream);
+
+/* number of launches of this library's kernels queued since the process
+ * started (host-side counter, incremented at every launch). */
+long long jmg_dev_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JMG_DEV_H */

@@ -1,0 +1,433 @@
+// jmg_api.cu -- C ABI and host-side drivers of the SPD solver.
+//
+// Paper: "Software design" -- the potrs workflow (Cholesky potrf followed by
+// potrs, optional log det) issued as one call on the framework's stream.
+//
+// Plain path (prec NATIVE, FP64): right-looking blocked Cholesky in place
+//   for each diagonal block k:  potf2 (FP64)  ->  panel TRSM (FP64)
+//                               ->  trailing SYRK update (FP64 CUDA cores)
+//   then blocked forward / back substitution.
+// Mixed path (prec BF16 / FP16): the same loop on an FP32 working copy W of
+//   lower(A) with FP64 diagonal blocks, an FP32 panel TRSM and tensor-core
+//   trailing updates on 16-bit split words; the FP32 factor then
+//   preconditions an FP64 refinement loop (residual in FP64 against the
+//   untouched A) until the normwise backward error reaches `tol`.
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "../../include/jmg_dev.h"
+#include "kernels.h"
+
+namespace jmg {
+
+// ---------------------------------------------------------------- workspace plan
+struct Plan {
+  size_t off_W = 0, off_PA = 0, off_PB = 0, off_X = 0, off_R = 0, off_D = 0, off_part = 0,
+         off_colmax = 0, off_eta = 0, off_anorm = 0, off_rowsum = 0, off_ints = 0, off_Z = 0,
+         off_P = 0, off_Q = 0, off_scal = 0, total = 0;
+  int ldw = 0, ldp = 0, kext = 0, splits = 1;
+};
+
+static void opts_or_default(const jmg_options* in, jmg_options* out) {
+  if (in)
+    *out = *in;
+  else
+    jmg_default_options(out);
+  if (out->nb <= 0) out->nb = 128;
+  if (out->NB <= 0) out->NB = out->nb;
+  if (out->words <= 0) out->words = 1;
+  if (out->words > 3) out->words = 3;
+  if (out->tol <= 0) out->tol = 1e-13;
+  if (out->maxit <= 0) out->maxit = 30;
+}
+
+static Plan plan_posv_mixed(int n, int nrhs, const jmg_options& o) {
+  Plan p;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off = round_up(off + bytes, 256);
+    return at;
+  };
+  const size_t N = (size_t)n, R = (size_t)(nrhs > 0 ? nrhs : 1);
+  p.ldw = (int)round_up(N > 0 ? N : 1, 32);
+  p.kext = o.nb * split_pairs(o.words);
+  p.ldp = (int)round_up((size_t)p.kext, 64);
+  p.splits = residual_splits(n, nrhs > 0 ? nrhs : 1);
+  p.off_W = take(sizeof(float) * (size_t)p.ldw * N);
+  p.off_PA = take(2 * N * p.ldp);
+  p.off_PB = take(2 * N * p.ldp);
+  p.off_X = take(sizeof(double) * N * R);
+  p.off_R = take(sizeof(double) * N * R);
+  p.off_D = take(sizeof(float) * N * R);
+  p.off_part = take(sizeof(double) * N * R * p.splits);
+  p.off_colmax = take(sizeof(double) * 3 * R);
+  p.off_eta = take(sizeof(double) * (1 + R));
+  p.off_anorm = take(sizeof(double) * 2);
+  p.off_rowsum = take(sizeof(double) * (N > 0 ? N : 1));
+  p.off_ints = take(sizeof(int) * 8);
+  p.off_Z = take(sizeof(double) * N * R);
+  p.off_P = take(sizeof(double) * N * R);
+  p.off_Q = take(sizeof(double) * N * R);
+  p.off_scal = take(sizeof(double) * 8 * R);
+  p.total = off;
+  return p;
+}
+
+template <typename T>
+static T* at(void* work, size_t off) {
+  return reinterpret_cast<T*>(reinterpret_cast<char*>(work) + off);
+}
+
+// ---------------------------------------------------------------- FP64 factor
+static int potrf_f64(int n, double* A, int lda, int nb, int* info, cudaStream_t s) {
+  for (int k = 0; k < n; k += nb) {
+    const int kb = std::min(nb, n - k);
+    double* Akk = A + (size_t)k * lda + k;
+    JMG_TRY(launch_potf2(Akk, lda, kb, k, info, s));
+    const int m = n - k - kb;
+    if (m <= 0) break;
+    double* L21 = Akk + kb;
+    JMG_TRY(launch_trsm(L21, lda, m, kb, Akk, info, s));
+    JMG_TRY(launch_gemm<double>(m, m, kb, L21, lda, MODE_N, L21, lda, MODE_T,
+                                A + (size_t)(k + kb) * lda + (k + kb), lda, OUT_SUB_LOWER, 1, info,
+                                s));
+  }
+  return JMG_OK;
+}
+
+// ---------------------------------------------------------------- mixed factor
+// Factor the FP32 working matrix W (lower) in place; info_f and err are device
+// ints of the workspace.
+static int factor_mixed(int n, float* W, int ldw, const jmg_options& o, const Plan& p,
+                        void* work, int* info_f, int* err, cudaStream_t s) {
+  const int nb = o.nb;
+  void* PA = at<void>(work, p.off_PA);
+  void* PB = split_pairs(o.words) > 1 ? at<void>(work, p.off_PB) : PA;
+  for (int k = 0; k < n; k += nb) {
+    const int kb = std::min(nb, n - k);
+    float* Wkk = W + (size_t)k * ldw + k;
+    JMG_TRY(launch_potf2(Wkk, ldw, kb, k, info_f, s));
+    const int m = n - k - kb;
+    if (m <= 0) break;
+    float* L21 = Wkk + kb;
+    JMG_TRY(launch_trsm(L21, ldw, m, kb, Wkk, info_f, s));
+    JMG_TRY(launch_split_words(m, kb, L21, ldw, o.prec, o.words, PA, PB, p.ldp, s));
+    JMG_TRY(launch_syrk_tc(m, kb * split_pairs(o.words), PA, PB, p.ldp, o.prec,
+                           W + (size_t)(k + kb) * ldw + (k + kb), ldw, err, s));
+  }
+  return JMG_OK;
+}
+
+// column max of |B| into colmax_r and R = B (start of refinement from X = 0)
+__global__ void k_copy_colmax(int n, const double* __restrict__ B, int ldb, double* __restrict__ R,
+                              double* __restrict__ colmax) {
+  const int c = blockIdx.y;
+  double m = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double v = B[(size_t)c * ldb + i];
+    R[(size_t)c * n + i] = v;
+    m = (isnan(v) || isnan(m)) ? NAN : fmax(m, fabs(v));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    double a = __shfl_xor_sync(0xffffffffu, m, o);
+    m = (isnan(a) || isnan(m)) ? NAN : fmax(m, a);
+  }
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&colmax[c], m);
+}
+
+static double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+static int sync_read(void* host, const void* dev, size_t bytes, cudaStream_t s) {
+  JMG_CUDA(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, s));
+  JMG_CUDA(cudaStreamSynchronize(s));
+  return JMG_OK;
+}
+
+// M^{-1} R in FP32 with per-column scaling, added to X (FP64): X += s * (L L^T)^{-1} (R / s)
+static int precond_update(int n, int nrhs, const float* W, int ldw, const double* R,
+                          const double* colmax_r, float* D, double* X, int nb, cudaStream_t s) {
+  JMG_TRY(launch_scale_to_f32(n, nrhs, R, n, colmax_r, D, n, s));
+  JMG_TRY(blocked_potrs<float>(n, nrhs, W, ldw, D, n, nb, nullptr, s));
+  JMG_TRY(launch_axpy_f32(n, nrhs, D, n, colmax_r, X, n, s));
+  return JMG_OK;
+}
+
+static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int ldb, int* info,
+                      const jmg_options& o, jmg_stats* st, void* work, cudaStream_t s) {
+  const Plan p = plan_posv_mixed(n, nrhs, o);
+  float* W = at<float>(work, p.off_W);
+  double* X = at<double>(work, p.off_X);
+  double* R = at<double>(work, p.off_R);
+  float* D = at<float>(work, p.off_D);
+  double* part = at<double>(work, p.off_part);
+  double* colmax = at<double>(work, p.off_colmax);
+  double* eta = at<double>(work, p.off_eta);
+  double* anorm = at<double>(work, p.off_anorm);
+  double* rowsum = at<double>(work, p.off_rowsum);
+  int* ints = at<int>(work, p.off_ints);  // [0] info_f, [1] err
+  jmg_stats local{};
+  jmg_stats& S = st ? *st : local;
+  S = jmg_stats{};
+  S.words_used = o.words;
+  S.refine_used = JMG_REFINE_IR;
+
+  double t0 = now_ms();
+  JMG_TRY(launch_norm_inf(n, A, lda, rowsum, anorm, s));
+  double anorm_h = 0;
+  JMG_TRY(sync_read(&anorm_h, anorm, sizeof(double), s));
+  S.anorm = anorm_h;
+
+  // factor, retrying with a diagonal shift when the low-precision factor breaks down
+  double shift = 0.0;
+  int hs[2] = {0, 0};
+  const double u_eff = (o.prec == JMG_PREC_FP16 ? std::ldexp(1.0, -11) : std::ldexp(1.0, -8));
+  const double u_words = std::pow(u_eff, o.words) + std::ldexp(1.0, -24);
+  for (int tries = 0;; ++tries) {
+    JMG_CUDA(cudaMemsetAsync(ints, 0, sizeof(int) * 8, s));
+    JMG_TRY(launch_lower_to_f32(n, A, lda, W, p.ldw, shift, s));
+    JMG_TRY(factor_mixed(n, W, p.ldw, o, p, work, &ints[0], &ints[1], s));
+    JMG_TRY(sync_read(hs, ints, sizeof(int) * 2, s));
+    S.factor_tries = tries + 1;
+    if (hs[1]) return S.status = JMG_ERR_TIMEOUT;
+    if (hs[0] == 0) break;
+    if (!o.shift_retry || tries >= 4) {
+      JMG_CUDA(cudaMemcpyAsync(info, &ints[0], sizeof(int), cudaMemcpyDeviceToDevice, s));
+      S.info = hs[0];
+      return S.status = JMG_ERR_NOT_SPD;
+    }
+    shift = (shift == 0.0) ? 4.0 * u_words * anorm_h : shift * 8.0;
+  }
+  S.shift = shift;
+  JMG_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
+  double t1 = now_ms();
+  S.t_factor_ms = t1 - t0;
+
+  // initial solve X = M^{-1} B
+  JMG_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)n * nrhs, s));
+  JMG_CUDA(cudaMemsetAsync(colmax, 0, sizeof(double) * 3 * nrhs, s));
+  {
+    dim3 grid(std::min(cdiv(n, 256), 64), nrhs);
+    k_copy_colmax<<<grid, 256, 0, s>>>(n, B, ldb, R, colmax);
+    JMG_TRY(launched());
+  }
+  JMG_TRY(precond_update(n, nrhs, W, p.ldw, R, colmax, D, X, o.nb, s));
+  double t2 = now_ms();
+
+  // FP64 iterative refinement
+  std::vector<double> eh(1 + nrhs);
+  double prev = INFINITY;
+  int stall = 0;
+  int it = 0;
+  for (;; ++it) {
+    JMG_TRY(launch_residual(n, nrhs, A, lda, X, n, B, ldb, R, n, colmax, part, p.splits, s));
+    JMG_TRY(launch_eta(nrhs, colmax, anorm, eta, s));
+    JMG_TRY(sync_read(eh.data(), eta, sizeof(double) * (1 + nrhs), s));
+    S.bwd_err = eh[0];
+    if (eh[0] <= o.tol) break;
+    if (it >= o.maxit || std::isnan(eh[0])) {
+      S.status = JMG_ERR_NOT_CONVERGED;
+      break;
+    }
+    stall = (eh[0] > 0.5 * prev) ? stall + 1 : 0;
+    if (stall >= 3) {
+      S.status = JMG_ERR_NOT_CONVERGED;
+      break;
+    }
+    prev = eh[0];
+    JMG_TRY(precond_update(n, nrhs, W, p.ldw, R, colmax, D, X, o.nb, s));
+  }
+  S.iters = it;
+  JMG_TRY(launch_copy2d(n, nrhs, X, n, B, ldb, s));
+  JMG_CUDA(cudaStreamSynchronize(s));
+  double t3 = now_ms();
+  S.t_solve_ms = t2 - t1;
+  S.t_refine_ms = t3 - t2;
+  return S.status;
+}
+
+static int check_common(int n, int lda, int dtype) {
+  if (n < 0) return -1;
+  if (lda < std::max(1, n)) return -3;
+  if (dtype != JMG_F64 && dtype != JMG_F32) return -4;
+  return JMG_OK;
+}
+
+}  // namespace jmg
+
+using namespace jmg;
+
+extern "C" {
+
+void jmg_default_options(jmg_options* o) {
+  if (!o) return;
+  o->nb = 128;
+  o->NB = 128;
+  o->prec = JMG_PREC_NATIVE;
+  o->words = 1;
+  o->tol = 1e-13;
+  o->maxit = 30;
+  o->refine = JMG_REFINE_AUTO;
+  o->shift_retry = 1;
+}
+
+size_t jmg_workspace_size(int op, int n, int nrhs, int dtype, const jmg_options* opt) {
+  (void)dtype;
+  jmg_options o;
+  opts_or_default(opt, &o);
+  if (op == JMG_OP_POSV && o.prec != JMG_PREC_NATIVE && n > 0)
+    return plan_posv_mixed(n, nrhs, o).total;
+  return 0;
+}
+
+const char* jmg_status_string(int st) {
+  switch (st) {
+    case JMG_OK: return "ok";
+    case JMG_ERR_CUDA: return "CUDA error";
+    case JMG_ERR_WORKSPACE: return "workspace too small";
+    case JMG_ERR_NOT_SPD: return "matrix is not positive definite";
+    case JMG_ERR_NOT_CONVERGED: return "refinement did not reach the tolerance";
+    case JMG_ERR_TIMEOUT: return "device-side wait timed out";
+    case JMG_ERR_UNSUPPORTED: return "unsupported option combination";
+    case JMG_ERR_ALIGN: return "alignment requirement not met";
+    default: return st < 0 ? "illegal argument" : "unknown status";
+  }
+}
+
+int jmg_potrf(int n, void* A, int lda, int dtype, int* info, const jmg_options* opt, void* work,
+              size_t lwork, void* stream) {
+  (void)work;
+  (void)lwork;
+  JMG_TRY(check_common(n, lda, dtype));
+  if (!info) return -5;
+  if (n > 0 && !A) return -2;
+  jmg_options o;
+  opts_or_default(opt, &o);
+  if (o.nb != 64 && o.nb != 128) return -6;
+  if (o.prec != JMG_PREC_NATIVE || dtype != JMG_F64) return JMG_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  JMG_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
+  return potrf_f64(n, (double*)A, lda, o.nb, info, s);
+}
+
+int jmg_potrs(int n, int nrhs, const void* L, int lda, void* B, int ldb, int dtype, void* work,
+              size_t lwork, void* stream) {
+  (void)work;
+  (void)lwork;
+  if (n < 0) return -1;
+  if (nrhs < 0) return -2;
+  if (lda < std::max(1, n)) return -4;
+  if (ldb < std::max(1, n)) return -6;
+  if (dtype != JMG_F64) return dtype == JMG_F32 ? JMG_ERR_UNSUPPORTED : -7;
+  if (n == 0 || nrhs == 0) return JMG_OK;
+  if (!L) return -3;
+  if (!B) return -5;
+  return blocked_potrs<double>(n, nrhs, (const double*)L, lda, (double*)B, ldb, 128, nullptr,
+                               (cudaStream_t)stream);
+}
+
+int jmg_posv(int n, int nrhs, void* A, int lda, void* B, int ldb, int dtype, int* info,
+             const jmg_options* opt, jmg_stats* stats, void* work, size_t lwork, void* stream) {
+  if (n < 0) return -1;
+  if (nrhs < 0) return -2;
+  if (lda < std::max(1, n)) return -4;
+  if (ldb < std::max(1, n)) return -6;
+  if (dtype != JMG_F64) return dtype == JMG_F32 ? JMG_ERR_UNSUPPORTED : -7;
+  if (!info) return -8;
+  jmg_options o;
+  opts_or_default(opt, &o);
+  if (o.nb != 64 && o.nb != 128) return -9;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (stats) *stats = jmg_stats{};
+  if (n == 0) {
+    JMG_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
+    return JMG_OK;
+  }
+  if (!A) return -3;
+  if (nrhs > 0 && !B) return -5;
+  if (o.prec == JMG_PREC_NATIVE) {
+    JMG_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
+    JMG_TRY(potrf_f64(n, (double*)A, lda, o.nb, info, s));
+    if (nrhs > 0)
+      JMG_TRY(blocked_potrs<double>(n, nrhs, (const double*)A, lda, (double*)B, ldb, o.nb, info,
+                                    s));
+    return JMG_OK;
+  }
+  if (o.prec != JMG_PREC_BF16 && o.prec != JMG_PREC_FP16) return JMG_ERR_UNSUPPORTED;
+  if (nrhs == 0) return JMG_OK;
+  size_t need = plan_posv_mixed(n, nrhs, o).total;
+  if (!work || lwork < need) return JMG_ERR_WORKSPACE;
+  if (reinterpret_cast<uintptr_t>(work) & 255) return JMG_ERR_ALIGN;
+  return posv_mixed(n, nrhs, (const double*)A, lda, (double*)B, ldb, info, o, stats, work, s);
+}
+
+__global__ void k_logdet(int n, const double* __restrict__ L, int lda, double* __restrict__ out) {
+  // one CTA, fixed-order reduction
+  __shared__ double part[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += log(L[(size_t)i * lda + i]);
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = 2.0 * part[0];
+}
+
+int jmg_logdet(int n, const void* L, int lda, int dtype, double* out, void* stream) {
+  if (n < 0) return -1;
+  if (lda < std::max(1, n)) return -3;
+  if (dtype != JMG_F64) return JMG_ERR_UNSUPPORTED;
+  if (!out) return -5;
+  if (n > 0 && !L) return -2;
+  k_logdet<<<1, 256, 0, (cudaStream_t)stream>>>(n, (const double*)L, lda, out);
+  return launched();
+}
+
+// ---------------------------------------------------------------- dev entry points
+int jmg_dev_syrk_tc(int m, int kext, const void* PA, const void* PB, int ldp, int prec, float* C,
+                    int ldc, int* err, void* stream) {
+  if (m < 0) return -1;
+  if (ldc < std::max(1, m)) return -8;
+  if (!err) return -9;
+  return launch_syrk_tc(m, kext, PA, PB, ldp, prec, C, ldc, err, (cudaStream_t)stream);
+}
+
+int jmg_dev_syrk_fp8(int m, int kext, const void* Q, int ldq, const signed char* e, float* C,
+                     int ldc, int* err, void* stream) {
+  if (m < 0) return -1;
+  if (ldc < std::max(1, m)) return -7;
+  if (!err) return -8;
+  return launch_syrk_fp8(m, kext, Q, ldq, e, C, ldc, err, (cudaStream_t)stream);
+}
+
+size_t jmg_dev_residual_workspace(int n, int nrhs) {
+  if (n <= 0 || nrhs <= 0) return 0;
+  return sizeof(double) * (size_t)n * nrhs * residual_splits(n, nrhs);
+}
+
+int jmg_dev_residual(int n, int nrhs, const double* A, int lda, const double* X, int ldx,
+                     const double* B, int ldb, double* R, int ldr, double* colmax, void* work,
+                     size_t lwork, void* stream) {
+  if (n < 0) return -1;
+  if (nrhs < 0) return -2;
+  if (lwork < jmg_dev_residual_workspace(n, nrhs)) return JMG_ERR_WORKSPACE;
+  return launch_residual(n, nrhs, A, lda, X, ldx, B, ldb, R, ldr, colmax, (double*)work,
+                         residual_splits(n, nrhs), (cudaStream_t)stream);
+}
+
+int jmg_dev_norm_inf(int n, const double* A, int lda, double* out, void* work, size_t lwork,
+                     void* stream) {
+  if (n < 0) return -1;
+  if (lwork < sizeof(double) * (size_t)std::max(n, 1)) return JMG_ERR_WORKSPACE;
+  return launch_norm_inf(n, A, lda, (double*)work, out, (cudaStream_t)stream);
+}
+
+long long jmg_dev_launch_count(void) { return g_launches; }
+
+}  // extern "C"

@@ -1,0 +1,714 @@
+// k_dense.cu -- CUDA-core kernels of the blocked Cholesky solver (sm_103a):
+// diagonal-block factorisation, panel TRSM, tiled GEMM / SYRK / SYMM, blocked
+// triangular solves, FP64 residual and the small helpers of the refinement loop.
+//
+// Paper: "Software design" -- potrs solves A x = b for SPD A by a Cholesky
+// factorisation followed by the triangular solves.  The paper delegates both to
+// cuSOLVERMp; the blocking below is the textbook right-looking scheme (factor
+// the diagonal block, solve the panel below it, update the trailing matrix).
+#include "kernels.h"
+
+namespace jmg {
+
+long long g_launches = 0;
+
+// ============================================================================
+// potf2: Cholesky of one diagonal block (kb <= NBMAX) in shared memory, FP64.
+// Storage type T (double: plain path; float: the FP32 working matrix of the
+// mixed path).  Right-looking within the block: pivot, scale the column,
+// rank-1 update of the remaining lower triangle.  On a pivot that is not > 0
+// (or NaN) it records info = koff + j + 1 and stops; the partly factored
+// block is written back, as LAPACK does.
+// ============================================================================
+template <typename T, int NBMAX>
+__global__ void __launch_bounds__(256) k_potf2(T* __restrict__ A, int lda, int kb, int koff,
+                                               int* __restrict__ info) {
+  extern __shared__ double sm_potf2[];
+  __shared__ int fail;
+  if (*(volatile int*)info != 0) return;  // an earlier block already failed
+  const int ld = kb + 1;
+  double* s = sm_potf2;
+  const int t = threadIdx.x;
+  for (int idx = t; idx < kb * kb; idx += blockDim.x) {
+    int i = idx % kb, j = idx / kb;
+    if (i >= j) s[j * ld + i] = (double)A[(size_t)j * lda + i];
+  }
+  if (t == 0) fail = 0;
+  __syncthreads();
+  constexpr int G = 256 / NBMAX;  // column groups
+  const int r = t % NBMAX, g = t / NBMAX;
+  for (int j = 0; j < kb; ++j) {
+    if (t == 0) {
+      double d = s[j * ld + j];
+      if (!(d > 0.0))
+        fail = j + 1;
+      else
+        s[j * ld + j] = sqrt(d);
+    }
+    __syncthreads();
+    if (fail) break;
+    const double ljj = s[j * ld + j];
+    if (g == 0 && r > j && r < kb) s[j * ld + r] = s[j * ld + r] / ljj;
+    __syncthreads();
+    if (r > j && r < kb) {
+      const double lrj = s[j * ld + r];
+      for (int c = j + 1 + g; c <= r; c += G) s[c * ld + r] -= lrj * s[j * ld + c];
+    }
+    __syncthreads();
+  }
+  for (int idx = t; idx < kb * kb; idx += blockDim.x) {
+    int i = idx % kb, j = idx / kb;
+    if (i >= j) A[(size_t)j * lda + i] = (T)s[j * ld + i];
+  }
+  if (t == 0 && fail) atomicCAS(info, 0, koff + fail);
+}
+
+template <typename T>
+static int potf2_impl(T* A, int lda, int kb, int koff, int* info, cudaStream_t s) {
+  size_t smem = (size_t)kb * (kb + 1) * sizeof(double);
+  if (kb <= 64) {
+    auto k = k_potf2<T, 64>;
+    JMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k<<<1, 256, smem, s>>>(A, lda, kb, koff, info);
+  } else {
+    auto k = k_potf2<T, 128>;
+    JMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k<<<1, 256, smem, s>>>(A, lda, kb, koff, info);
+  }
+  return launched();
+}
+int launch_potf2(double* A, int lda, int kb, int koff, int* info, cudaStream_t s) {
+  return potf2_impl(A, lda, kb, koff, info, s);
+}
+int launch_potf2(float* A, int lda, int kb, int koff, int* info, cudaStream_t s) {
+  return potf2_impl(A, lda, kb, koff, info, s);
+}
+
+// ============================================================================
+// Panel TRSM: A21 (m x kb) <- A21 * Lkk^{-T}, in place.  Each CTA owns BR rows;
+// row r of the result solves x_r Lkk^T = a_r by forward substitution over the
+// columns j (x_rj = a_rj / L_jj, then a_rl -= x_rj L_lj for l > j).  Lkk sits in
+// shared memory; threads are (row, column-group) pairs.
+// ============================================================================
+template <typename T, int BR>
+__global__ void __launch_bounds__(256) k_trsm(T* __restrict__ A21, int lda, int m, int kb,
+                                              const T* __restrict__ Lkk,
+                                              const int* __restrict__ info) {
+  if (*(volatile const int*)info != 0) return;
+  extern __shared__ __align__(16) unsigned char sm_trsm[];
+  T* Ls = reinterpret_cast<T*>(sm_trsm);  // kb x (kb+1), column-major
+  const int ldl = kb + 1;
+  T* Xs = Ls + (size_t)kb * ldl;  // kb columns x (BR+1)
+  const int ldx = BR + 1;
+  const int t = threadIdx.x;
+  const int r0 = blockIdx.x * BR;
+  for (int idx = t; idx < kb * kb; idx += blockDim.x) {
+    int i = idx % kb, j = idx / kb;
+    Ls[j * ldl + i] = (i >= j) ? Lkk[(size_t)j * lda + i] : T(0);
+  }
+  for (int idx = t; idx < BR * kb; idx += blockDim.x) {
+    int i = idx % BR, j = idx / BR;
+    Xs[j * ldx + i] = (r0 + i < m) ? A21[(size_t)j * lda + r0 + i] : T(0);
+  }
+  __syncthreads();
+  constexpr int G = 256 / BR;
+  const int r = t % BR, g = t / BR;
+  for (int j = 0; j < kb; ++j) {
+    if (g == 0) Xs[j * ldx + r] = Xs[j * ldx + r] / Ls[j * ldl + j];
+    __syncthreads();
+    const T xrj = Xs[j * ldx + r];
+    for (int l = j + 1 + g; l < kb; l += G) Xs[l * ldx + r] -= xrj * Ls[j * ldl + l];
+    __syncthreads();
+  }
+  for (int idx = t; idx < BR * kb; idx += blockDim.x) {
+    int i = idx % BR, j = idx / BR;
+    if (r0 + i < m) A21[(size_t)j * lda + r0 + i] = Xs[j * ldx + i];
+  }
+}
+
+template <typename T, int BR>
+static int trsm_impl(T* A21, int lda, int m, int kb, const T* Lkk, const int* info,
+                     cudaStream_t s) {
+  if (m <= 0) return JMG_OK;
+  size_t smem = ((size_t)kb * (kb + 1) + (size_t)kb * (BR + 1)) * sizeof(T);
+  auto k = k_trsm<T, BR>;
+  JMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k<<<cdiv(m, BR), 256, smem, s>>>(A21, lda, m, kb, Lkk, info);
+  return launched();
+}
+int launch_trsm(double* A21, int lda, int m, int kb, const double* Lkk, const int* info,
+                cudaStream_t s) {
+  return trsm_impl<double, 32>(A21, lda, m, kb, Lkk, info, s);
+}
+int launch_trsm(float* A21, int lda, int m, int kb, const float* Lkk, const int* info,
+                cudaStream_t s) {
+  return trsm_impl<float, 64>(A21, lda, m, kb, Lkk, info, s);
+}
+
+// ============================================================================
+// Tiled GEMM on the CUDA cores: C -= op(A) op(B) with 64 x BN output tiles,
+// BK = 16, 256 threads, each thread a 4 x (BN/16) register tile.  Rows of a
+// thread are tx + 16 q and columns ty + 16 q' so that shared-memory reads are
+// conflict-free and global stores coalesce along a column.
+// ============================================================================
+constexpr int GBM = 64, GBK = 16;
+
+template <typename T, int AMODE>
+JMG_DEV T load_a(const T* __restrict__ A, int lda, int i, int l) {
+  if (AMODE == MODE_N) return A[(size_t)l * lda + i];
+  if (AMODE == MODE_T) return A[(size_t)i * lda + l];
+  return (i >= l) ? A[(size_t)l * lda + i] : A[(size_t)i * lda + l];
+}
+
+template <typename T, int BN, int AMODE, int BMODE, int OUT>
+__global__ void __launch_bounds__(256) k_gemm(int m, int n, int k, const T* __restrict__ A, int lda,
+                                              const T* __restrict__ B, int ldb, T* __restrict__ C,
+                                              int ldc, int kchunk, const int* __restrict__ info) {
+  if (info && *(volatile const int*)info != 0) return;
+  constexpr int TN = BN / 16;
+  __shared__ T As[GBK][GBM + 1];
+  __shared__ T Bs[GBK][BN + 1];
+  int ti, tj;
+  if (OUT == OUT_SUB_LOWER) {
+    tri_index(blockIdx.x, ti, tj);
+  } else {
+    ti = blockIdx.x;
+    tj = blockIdx.y;
+  }
+  const int i0 = ti * GBM, j0 = tj * BN;
+  const int kbeg = (OUT == OUT_PART) ? blockIdx.z * kchunk : 0;
+  const int kend = (OUT == OUT_PART) ? min(k, kbeg + kchunk) : k;
+  const int t = threadIdx.x, tx = t % 16, ty = t / 16;
+  T acc[4][TN];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int p = 0; p < TN; ++p) acc[q][p] = T(0);
+
+  for (int l0 = kbeg; l0 < kend; l0 += GBK) {
+    // ---- A tile: GBM x GBK
+    // coalesce along the stored column: rows for N (and S tiles that reach the
+    // lower triangle), k for T (and S tiles wholly above the diagonal)
+    const bool a_rowfast = (AMODE == MODE_N) || (AMODE == MODE_S && !(i0 + GBM - 1 < l0));
+#pragma unroll
+    for (int q = 0; q < (GBM * GBK) / 256; ++q) {
+      int idx = t + 256 * q;
+      int ii, ll;
+      if (a_rowfast) {
+        ii = idx % GBM;
+        ll = idx / GBM;
+      } else {
+        ll = idx % GBK;
+        ii = idx / GBK;
+      }
+      int gi = i0 + ii, gl = l0 + ll;
+      As[ll][ii] = (gi < m && gl < kend) ? load_a<T, AMODE>(A, lda, gi, gl) : T(0);
+    }
+    // ---- B tile: GBK x BN
+#pragma unroll
+    for (int q = 0; q < (GBK * BN + 255) / 256; ++q) {
+      int idx = t + 256 * q;
+      if (idx < GBK * BN) {
+        int ll, jj;
+        if (BMODE == MODE_N) {
+          ll = idx % GBK;
+          jj = idx / GBK;
+        } else {
+          jj = idx % BN;
+          ll = idx / BN;
+        }
+        int gl = l0 + ll, gj = j0 + jj;
+        T v = T(0);
+        if (gl < kend && gj < n)
+          v = (BMODE == MODE_N) ? B[(size_t)gj * ldb + gl] : B[(size_t)gl * ldb + gj];
+        Bs[ll][jj] = v;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < GBK; ++l) {
+      T a[4], b[TN];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a[q] = As[l][tx + 16 * q];
+#pragma unroll
+      for (int p = 0; p < TN; ++p) b[p] = Bs[l][ty + 16 * p];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int p = 0; p < TN; ++p) acc[q][p] = fma(a[q], b[p], acc[q][p]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int gi = i0 + tx + 16 * q;
+    if (gi >= m) continue;
+#pragma unroll
+    for (int p = 0; p < TN; ++p) {
+      int gj = j0 + ty + 16 * p;
+      if (gj >= n) continue;
+      if (OUT == OUT_PART) {
+        C[(size_t)blockIdx.z * ldc * n + (size_t)gj * ldc + gi] = acc[q][p];
+      } else {
+        if (OUT == OUT_SUB_LOWER && gi < gj) continue;
+        C[(size_t)gj * ldc + gi] -= acc[q][p];
+      }
+    }
+  }
+}
+
+template <typename T, int BN, int AMODE, int BMODE, int OUT>
+static int gemm_launch4(int m, int n, int k, const T* A, int lda, const T* B, int ldb, T* C,
+                        int ldc, int splits, const int* info, cudaStream_t s) {
+  dim3 grid;
+  int kchunk = k;
+  if (OUT == OUT_SUB_LOWER) {
+    long long tiles = tri_tiles(cdiv(m, GBM));
+    grid = dim3((unsigned)tiles, 1, 1);
+  } else {
+    grid = dim3(cdiv(m, GBM), cdiv(n, BN), 1);
+    if (OUT == OUT_PART) {
+      kchunk = (int)round_up((size_t)cdiv(k, splits), GBK);
+      grid.z = cdiv(k, kchunk);
+    }
+  }
+  k_gemm<T, BN, AMODE, BMODE, OUT><<<grid, 256, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, kchunk,
+                                                        info);
+  return launched();
+}
+
+template <typename T, int AMODE, int BMODE, int OUT>
+static int gemm_bn(int m, int n, int k, const T* A, int lda, const T* B, int ldb, T* C, int ldc,
+                   int splits, const int* info, cudaStream_t s) {
+  if (OUT == OUT_SUB_LOWER || n > 32)
+    return gemm_launch4<T, 64, AMODE, BMODE, OUT>(m, n, k, A, lda, B, ldb, C, ldc, splits, info, s);
+  if (n > 16)
+    return gemm_launch4<T, 32, AMODE, BMODE, OUT>(m, n, k, A, lda, B, ldb, C, ldc, splits, info, s);
+  return gemm_launch4<T, 16, AMODE, BMODE, OUT>(m, n, k, A, lda, B, ldb, C, ldc, splits, info, s);
+}
+
+template <typename T>
+int launch_gemm(int m, int n, int k, const T* A, int lda, int amode, const T* B, int ldb,
+                int bmode, T* C, int ldc, int out, int splits, const int* info, cudaStream_t s) {
+  if (m <= 0 || n <= 0 || k <= 0) return JMG_OK;
+#define JMG_G(AM, BM, OU) \
+  if (amode == AM && bmode == BM && out == OU) \
+    return gemm_bn<T, AM, BM, OU>(m, n, k, A, lda, B, ldb, C, ldc, splits, info, s);
+  JMG_G(MODE_N, MODE_T, OUT_SUB_LOWER)  // SYRK: C -= P P^T
+  JMG_G(MODE_N, MODE_N, OUT_SUB)        // forward-solve update: B -= L Y
+  JMG_G(MODE_T, MODE_N, OUT_SUB)        // back-solve update: B -= L^T X
+  JMG_G(MODE_S, MODE_N, OUT_PART)       // symmetric residual partials
+  JMG_G(MODE_N, MODE_T, OUT_SUB)        // general C -= A B^T
+#undef JMG_G
+  return JMG_ERR_UNSUPPORTED;
+}
+template int launch_gemm<double>(int, int, int, const double*, int, int, const double*, int, int,
+                                 double*, int, int, int, const int*, cudaStream_t);
+template int launch_gemm<float>(int, int, int, const float*, int, int, const float*, int, int,
+                                float*, int, int, int, const int*, cudaStream_t);
+
+// ============================================================================
+// Diagonal-block triangular solve, one warp per right-hand side.  Lane l holds
+// rows l, l+32, l+64, l+96 of its column.  Forward (L y = b): for each j the
+// owner lane divides by L_jj, broadcasts y_j, every lane updates its rows below
+// j.  Backward (L^T x = y): j descends, the update runs over rows above j with
+// row j of L (L^T's column j).
+// ============================================================================
+template <typename T, int NBMAX>
+__global__ void __launch_bounds__(256) k_trsv_diag(int kb, int nrhs, const T* __restrict__ L,
+                                                   int lda, T* __restrict__ B, int ldb, int trans,
+                                                   const int* __restrict__ info) {
+  if (info && *(volatile const int*)info != 0) return;
+  extern __shared__ __align__(16) unsigned char sm_trsv[];
+  T* Ls = reinterpret_cast<T*>(sm_trsv);
+  const int ld = kb + 1;
+  for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
+    int i = idx % kb, j = idx / kb;
+    Ls[j * ld + i] = (i >= j) ? L[(size_t)j * lda + i] : T(0);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int col = blockIdx.x * 8 + warp;
+  if (col >= nrhs) return;
+  constexpr int Q = NBMAX / 32;
+  T b[Q];
+  T* bc = B + (size_t)col * ldb;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    int r = lane + 32 * q;
+    b[q] = (r < kb) ? bc[r] : T(0);
+  }
+  if (trans == 0) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      for (int jj = 0; jj < 32; ++jj) {
+        const int j = q * 32 + jj;
+        if (j >= kb) break;
+        if (lane == jj) b[q] = b[q] / Ls[j * ld + j];
+        const T y = __shfl_sync(0xffffffffu, b[q], jj);
+#pragma unroll
+        for (int p = q; p < Q; ++p) {
+          int r = lane + 32 * p;
+          if (r > j && r < kb) b[p] -= Ls[j * ld + r] * y;
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int q = Q - 1; q >= 0; --q) {
+      for (int jj = 31; jj >= 0; --jj) {
+        const int j = q * 32 + jj;
+        if (j >= kb) continue;
+        if (lane == jj) b[q] = b[q] / Ls[j * ld + j];
+        const T x = __shfl_sync(0xffffffffu, b[q], jj);
+#pragma unroll
+        for (int p = 0; p <= q; ++p) {
+          int r = lane + 32 * p;
+          if (r < j) b[p] -= Ls[r * ld + j] * x;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    int r = lane + 32 * q;
+    if (r < kb) bc[r] = b[q];
+  }
+}
+
+template <typename T>
+int launch_trsv_diag(int kb, int nrhs, const T* L, int lda, T* B, int ldb, int trans,
+                     const int* info, cudaStream_t s) {
+  if (kb <= 0 || nrhs <= 0) return JMG_OK;
+  size_t smem = (size_t)kb * (kb + 1) * sizeof(T);
+  dim3 grid(cdiv(nrhs, 8));
+  if (kb <= 64) {
+    auto k = k_trsv_diag<T, 64>;
+    JMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k<<<grid, 256, smem, s>>>(kb, nrhs, L, lda, B, ldb, trans, info);
+  } else {
+    auto k = k_trsv_diag<T, 128>;
+    JMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k<<<grid, 256, smem, s>>>(kb, nrhs, L, lda, B, ldb, trans, info);
+  }
+  return launched();
+}
+template int launch_trsv_diag<double>(int, int, const double*, int, double*, int, int, const int*,
+                                      cudaStream_t);
+template int launch_trsv_diag<float>(int, int, const float*, int, float*, int, int, const int*,
+                                     cudaStream_t);
+
+// Blocked right-looking solves: forward over diagonal blocks with a GEMM update
+// of the rows below, then backward with a GEMM update of the rows above.
+template <typename T>
+int blocked_potrs(int n, int nrhs, const T* L, int lda, T* B, int ldb, int nb, const int* info,
+                  cudaStream_t s) {
+  for (int k = 0; k < n; k += nb) {
+    int kb = min(nb, n - k);
+    JMG_TRY(launch_trsv_diag<T>(kb, nrhs, L + (size_t)k * lda + k, lda, B + k, ldb, 0, info, s));
+    int m = n - k - kb;
+    if (m > 0)
+      JMG_TRY(launch_gemm<T>(m, nrhs, kb, L + (size_t)k * lda + k + kb, lda, MODE_N, B + k, ldb,
+                             MODE_N, B + k + kb, ldb, OUT_SUB, 1, info, s));
+  }
+  int last = ((n - 1) / nb) * nb;
+  for (int k = last; k >= 0; k -= nb) {
+    int kb = min(nb, n - k);
+    JMG_TRY(launch_trsv_diag<T>(kb, nrhs, L + (size_t)k * lda + k, lda, B + k, ldb, 1, info, s));
+    if (k > 0)  // B[0:k] -= L[k:k+kb, 0:k]^T X_k
+      JMG_TRY(launch_gemm<T>(k, nrhs, kb, L + k, lda, MODE_T, B + k, ldb, MODE_N, B, ldb,
+                             OUT_SUB, 1, info, s));
+  }
+  return JMG_OK;
+}
+template int blocked_potrs<double>(int, int, const double*, int, double*, int, int, const int*,
+                                   cudaStream_t);
+template int blocked_potrs<float>(int, int, const float*, int, float*, int, int, const int*,
+                                  cudaStream_t);
+
+// ============================================================================
+// FP64 residual R = B - A X (A symmetric, lower stored): split-K partial sums of
+// A X through the tiled GEMM (mode S), then a fixed-order reduction that also
+// records the per-column infinity norms of r, x and b.
+// ============================================================================
+int residual_splits(int n, int nrhs) {
+  // enough CTAs for ~8 per SM on 152 SMs, never chunks shorter than 256
+  long long tiles = (long long)cdiv(n, GBM) * cdiv(nrhs, nrhs > 32 ? 64 : (nrhs > 16 ? 32 : 16));
+  long long want = 152LL * 8;
+  int splits = (int)((want + tiles - 1) / tiles);
+  int maxs = max(1, n / 256);
+  return max(1, min(splits, maxs));
+}
+
+__global__ void k_resid_reduce(int n, int nrhs, int splits, const double* __restrict__ part,
+                               const double* __restrict__ X, int ldx, const double* __restrict__ B,
+                               int ldb, double* __restrict__ R, int ldr, double* __restrict__ colmax) {
+  const int c = blockIdx.y;
+  double rm = 0.0, xm = 0.0, bm = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int z = 0; z < splits; ++z) acc += part[(size_t)z * n * nrhs + (size_t)c * n + i];
+    double b = B[(size_t)c * ldb + i];
+    double r = b - acc;
+    R[(size_t)c * ldr + i] = r;
+    double x = X[(size_t)c * ldx + i];
+    rm = (isnan(r) || isnan(rm)) ? NAN : fmax(rm, fabs(r));
+    xm = (isnan(x) || isnan(xm)) ? NAN : fmax(xm, fabs(x));
+    bm = fmax(bm, fabs(b));
+  }
+  // warp then block max
+  for (int o = 16; o > 0; o >>= 1) {
+    double a = __shfl_xor_sync(0xffffffffu, rm, o);
+    rm = (isnan(a) || isnan(rm)) ? NAN : fmax(rm, a);
+    a = __shfl_xor_sync(0xffffffffu, xm, o);
+    xm = (isnan(a) || isnan(xm)) ? NAN : fmax(xm, a);
+    bm = fmax(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg(&colmax[c], rm);
+    atomic_max_nonneg(&colmax[nrhs + c], xm);
+    atomic_max_nonneg(&colmax[2 * nrhs + c], bm);
+  }
+}
+
+int launch_residual(int n, int nrhs, const double* A, int lda, const double* X, int ldx,
+                    const double* B, int ldb, double* R, int ldr, double* colmax, double* part,
+                    int splits, cudaStream_t s) {
+  if (n <= 0 || nrhs <= 0) return JMG_OK;
+  JMG_CUDA(cudaMemsetAsync(colmax, 0, sizeof(double) * 3 * nrhs, s));
+  JMG_TRY(launch_gemm<double>(n, nrhs, n, A, lda, MODE_S, X, ldx, MODE_N, part, n, OUT_PART, splits,
+                              nullptr, s));
+  // number of splits actually used by the GEMM grid
+  int kchunk = (int)round_up((size_t)cdiv(n, splits), GBK);
+  int used = cdiv(n, kchunk);
+  dim3 grid(min(cdiv(n, 256), 64), nrhs);
+  k_resid_reduce<<<grid, 256, 0, s>>>(n, nrhs, used, part, X, ldx, B, ldb, R, ldr, colmax);
+  return launched();
+}
+
+// ||A||_inf from lower(A): each 64 x 64 lower tile adds |a_ij| to row i and,
+// below the diagonal, to row j (the mirrored entry).
+__global__ void k_rowsum_lower(int n, const double* __restrict__ A, int lda,
+                               double* __restrict__ rowsum) {
+  int ti, tj;
+  tri_index(blockIdx.x, ti, tj);
+  const int i0 = ti * 64, j0 = tj * 64;
+  const int tx = threadIdx.x % 64, ty = threadIdx.x / 64;  // 256 threads
+  const int i = i0 + tx;
+  double rs = 0.0;
+  double cs[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) cs[q] = 0.0;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    int j = j0 + ty * 16 + q;
+    if (i < n && j < n && i >= j) {
+      double v = fabs(A[(size_t)j * lda + i]);
+      rs += v;
+      if (i > j) cs[q] = v;
+    }
+  }
+  if (i < n) atomicAdd(&rowsum[i], rs);
+  // column sums over the 64 rows: reduce cs[q] across tx (64 threads = 2 warps)
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    double v = cs[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    cs[q] = v;
+  }
+  // lane 0 of each warp adds the partial column sums of its 32 rows
+  if ((tx & 31) == 0) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      int j = j0 + ty * 16 + q;
+      if (j < n && cs[q] != 0.0) atomicAdd(&rowsum[j], cs[q]);
+    }
+  }
+}
+
+__global__ void k_max_reduce(int n, const double* __restrict__ v, double* __restrict__ out) {
+  double m = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    m = (isnan(v[i]) || isnan(m)) ? NAN : fmax(m, v[i]);
+  for (int o = 16; o > 0; o >>= 1) {
+    double a = __shfl_xor_sync(0xffffffffu, m, o);
+    m = (isnan(a) || isnan(m)) ? NAN : fmax(m, a);
+  }
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
+}
+
+int launch_norm_inf(int n, const double* A, int lda, double* rowsum, double* out,
+                    cudaStream_t s) {
+  JMG_CUDA(cudaMemsetAsync(out, 0, sizeof(double), s));
+  if (n <= 0) return JMG_OK;
+  JMG_CUDA(cudaMemsetAsync(rowsum, 0, sizeof(double) * n, s));
+  k_rowsum_lower<<<(unsigned)tri_tiles(cdiv(n, 64)), 256, 0, s>>>(n, A, lda, rowsum);
+  JMG_TRY(launched());
+  k_max_reduce<<<min(cdiv(n, 256), 152), 256, 0, s>>>(n, rowsum, out);
+  return launched();
+}
+
+__global__ void k_eta(int nrhs, const double* __restrict__ colmax, const double* __restrict__ anorm,
+                      double* __restrict__ eta) {
+  // single warp
+  double worst = 0.0;
+  for (int c = threadIdx.x; c < nrhs; c += 32) {
+    double rn = colmax[c], xn = colmax[nrhs + c], bn = colmax[2 * nrhs + c];
+    double den = (*anorm) * xn + bn;
+    double e = den > 0.0 ? rn / den : (rn > 0.0 ? INFINITY : 0.0);
+    if (isnan(rn) || isnan(xn)) e = NAN;
+    eta[1 + c] = e;
+    worst = (isnan(e) || isnan(worst)) ? NAN : fmax(worst, e);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    double a = __shfl_xor_sync(0xffffffffu, worst, o);
+    worst = (isnan(a) || isnan(worst)) ? NAN : fmax(worst, a);
+  }
+  if (threadIdx.x == 0) eta[0] = worst;
+}
+
+int launch_eta(int nrhs, const double* colmax, const double* anorm, double* eta_out,
+               cudaStream_t s) {
+  k_eta<<<1, 32, 0, s>>>(nrhs, colmax, anorm, eta_out);
+  return launched();
+}
+
+// ============================================================================
+// Conversions used by the mixed-precision path.
+// ============================================================================
+__global__ void k_lower_to_f32(int n, const double* __restrict__ A, int lda, float* __restrict__ W,
+                               int ldw, double shift) {
+  // one CTA per column, rows j..n-1
+  const int j = blockIdx.x;
+  for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
+    double v = A[(size_t)j * lda + i];
+    if (i == j) v += shift;
+    W[(size_t)j * ldw + i] = (float)v;
+  }
+}
+
+int launch_lower_to_f32(int n, const double* A, int lda, float* W, int ldw, double shift,
+                        cudaStream_t s) {
+  if (n <= 0) return JMG_OK;
+  k_lower_to_f32<<<n, 256, 0, s>>>(n, A, lda, W, ldw, shift);
+  return launched();
+}
+
+// word pairs (a, b) with a + b < words, ordered by significance
+__constant__ int c_pair_a[6] = {0, 0, 1, 0, 1, 2};
+__constant__ int c_pair_b[6] = {0, 1, 0, 2, 1, 0};
+int split_pairs(int words) { return words <= 1 ? 1 : (words == 2 ? 3 : 6); }
+
+template <typename H>
+JMG_DEV H to16(float v);
+template <>
+JMG_DEV __nv_bfloat16 to16<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+template <>
+JMG_DEV __half to16<__half>(float v) {
+  return __float2half_rn(v);
+}
+template <typename H>
+JMG_DEV float from16(H v);
+template <>
+JMG_DEV float from16<__nv_bfloat16>(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+template <>
+JMG_DEV float from16<__half>(__half v) {
+  return __half2float(v);
+}
+
+// 32 x 32 tiles through shared memory: read down the stored columns of L21,
+// write along the rows of the row-major extended operands.
+template <typename H>
+__global__ void k_split_words(int m, int kb, const float* __restrict__ L21, int ldw, int npairs,
+                              H* __restrict__ PA, H* __restrict__ PB, int ldp) {
+  __shared__ float tile[32][33];
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int c = c0 + ty + 8 * q, r = r0 + tx;
+    tile[ty + 8 * q][tx] = (r < m && c < kb) ? L21[(size_t)c * ldw + r] : 0.0f;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int r = r0 + ty + 8 * q, c = c0 + tx;
+    if (r >= m || c >= kb) continue;
+    float rem = tile[tx][ty + 8 * q];
+    H w[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      w[u] = to16<H>(rem);
+      rem = rem - from16<H>(w[u]);
+    }
+    for (int p = 0; p < npairs; ++p) {
+      PA[(size_t)r * ldp + p * kb + c] = w[c_pair_a[p]];
+      if (PB) PB[(size_t)r * ldp + p * kb + c] = w[c_pair_b[p]];
+    }
+  }
+}
+
+int launch_split_words(int m, int kb, const float* L21, int ldw, int prec, int words, void* PA,
+                       void* PB, int ldp, cudaStream_t s) {
+  if (m <= 0) return JMG_OK;
+  int np = split_pairs(words);
+  dim3 grid(cdiv(m, 32), cdiv(kb, 32)), block(32, 8);
+  if (prec == JMG_PREC_FP16)
+    k_split_words<__half><<<grid, block, 0, s>>>(m, kb, L21, ldw, np, (__half*)PA,
+                                                 np > 1 ? (__half*)PB : nullptr, ldp);
+  else
+    k_split_words<__nv_bfloat16><<<grid, block, 0, s>>>(m, kb, L21, ldw, np, (__nv_bfloat16*)PA,
+                                                        np > 1 ? (__nv_bfloat16*)PB : nullptr,
+                                                        ldp);
+  return launched();
+}
+
+__global__ void k_scale_to_f32(int n, const double* __restrict__ R, int ldr,
+                               const double* __restrict__ colmax_r, float* __restrict__ D, int ldd) {
+  const int c = blockIdx.y;
+  double sc = colmax_r[c];
+  double inv = (sc > 0.0 && isfinite(sc)) ? 1.0 / sc : 1.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    D[(size_t)c * ldd + i] = (float)(R[(size_t)c * ldr + i] * inv);
+}
+
+int launch_scale_to_f32(int n, int nrhs, const double* R, int ldr, const double* colmax_r,
+                        float* D, int ldd, cudaStream_t s) {
+  dim3 grid(min(cdiv(n, 256), 64), nrhs);
+  k_scale_to_f32<<<grid, 256, 0, s>>>(n, R, ldr, colmax_r, D, ldd);
+  return launched();
+}
+
+__global__ void k_axpy_f32(int n, const float* __restrict__ D, int ldd,
+                           const double* __restrict__ colmax_r, double* __restrict__ X, int ldx) {
+  const int c = blockIdx.y;
+  double sc = colmax_r[c];
+  if (!(sc > 0.0 && isfinite(sc))) sc = 1.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    X[(size_t)c * ldx + i] += sc * (double)D[(size_t)c * ldd + i];
+}
+
+int launch_axpy_f32(int n, int nrhs, const float* D, int ldd, const double* colmax_r, double* X,
+                    int ldx, cudaStream_t s) {
+  dim3 grid(min(cdiv(n, 256), 64), nrhs);
+  k_axpy_f32<<<grid, 256, 0, s>>>(n, D, ldd, colmax_r, X, ldx);
+  return launched();
+}
+
+int launch_copy2d(int n, int nrhs, const double* src, int lds, double* dst, int ldd,
+                  cudaStream_t s) {
+  JMG_CUDA(cudaMemcpy2DAsync(dst, sizeof(double) * ldd, src, sizeof(double) * lds,
+                             sizeof(double) * n, nrhs, cudaMemcpyDeviceToDevice, s));
+  return JMG_OK;
+}
+
+int launch_zero(double* p, size_t n, cudaStream_t s) {
+  JMG_CUDA(cudaMemsetAsync(p, 0, sizeof(double) * n, s));
+  return JMG_OK;
+}
+
+}  // namespace jmg

@@ -1,0 +1,318 @@
+// k_tc.cu -- trailing-matrix update of the mixed-precision Cholesky factorisation
+// on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+//     C[i, j] -= sum_k PA[i, k] * PB[j, k]        (lower-triangle tiles only)
+//
+// PA / PB are the panel L21 split into 16-bit words (BF16 or FP16) and laid out
+// row-major, K contiguous, so both operands are "K-major".  With several words
+// the pairs (hi*hi, hi*lo, lo*hi, ...) are concatenated along K, so one GEMM with
+// K' = pairs * kb applies all of them to the same FP32 accumulator.
+//
+// One CTA per 128 x 128 output tile, 128 threads:
+//   warp 0 (one lane): TMA producer -- 128 x 64 tiles of PA and PB per stage,
+//                       128-byte swizzle, mbarrier transaction counts;
+//   warp 1 (one lane): MMA issuer   -- tcgen05.mma kind::f16, M=128 N=128 K=16,
+//                       FP32 accumulator in TMEM (128 lanes x 128 columns);
+//   all 4 warps:       epilogue     -- tcgen05.ld 32 lanes x 32 columns, then
+//                       C -= acc with coalesced column accesses (lane = row).
+// Every mbarrier wait is bounded (globaltimer); on expiry the kernel raises
+// *err, drains its own copies, frees TMEM and returns without touching C.
+//
+// The paper runs these updates inside cuSOLVERMp (FP32/FP64, "Software
+// design"); the split-word tensor-core form is this library's own design.
+#include <cuda.h>
+
+#include "kernels.h"
+
+namespace jmg {
+namespace tc {
+
+constexpr int BM = 128, BN = 128, BK = 64;  // BK: 64 x 16-bit = one 128-byte swizzle row
+constexpr int STAGES = 3;
+constexpr int TILE_BYTES = BM * BK * 2;  // 16 KiB
+constexpr int STAGE_BYTES = 2 * TILE_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr uint32_t TMEM_COLS = 128;
+constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s per wait: far above any legal wait
+
+// ---------------------------------------------------------------- PTX wrappers
+JMG_DEV void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+JMG_DEV void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+JMG_DEV void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+JMG_DEV void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+JMG_DEV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: true when the phase with `parity` completed, false on timeout.
+JMG_DEV bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > WAIT_NS) return false;
+  }
+}
+JMG_DEV void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+JMG_DEV void prefetch_tmap(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+JMG_DEV void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+}
+JMG_DEV void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+JMG_DEV void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+JMG_DEV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+JMG_DEV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+JMG_DEV void tc_mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+JMG_DEV void tc_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+JMG_DEV void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+JMG_DEV void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor for a K-major operand written by TMA with the
+// 128-byte swizzle: rows of 128 bytes, 8-row core groups 1024 bytes apart.
+JMG_DEV uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address, 16-byte units
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused with swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                    // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                    // swizzle mode: 128-byte
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A/B = BF16 (fmt 1) or F16 (fmt 0),
+// both K-major, no negation, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_f16(int m, int n, int ab_fmt) {
+  return (1u << 4) | ((uint32_t)ab_fmt << 7) | ((uint32_t)ab_fmt << 10) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(128, 1)
+    k_syrk_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              float* __restrict__ C, int ldc, int m, int kext, int ab_fmt, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char sm_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(sm_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  __shared__ int s_fail;
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  int ti, tj;
+  tri_index(blockIdx.x, ti, tj);
+  const int nk = kext / BK;
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    fence_mbar_init();
+    prefetch_tmap(&tmA);
+    prefetch_tmap(&tmB);
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  int issued = 0;  // producer: loads issued
+  if (warp == 0 && lane == 0) {
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1)) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
+      if (*(volatile int*)&s_fail) break;
+      unsigned char* sa = smem + s * STAGE_BYTES;
+      unsigned char* sb = sa + TILE_BYTES;
+      mbar_expect_tx(&full[s], STAGE_BYTES);
+      tma_load_2d(sa, &tmA, kb * BK, ti * BM, &full[s]);
+      tma_load_2d(sb, &tmB, kb * BK, tj * BN, &full[s]);
+      ++issued;
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = idesc_f16(BM, BN, ab_fmt);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(&full[s], (kb / STAGES) & 1)) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+      const uint32_t sb = sa + TILE_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        // K = 16 slice: 32 bytes further along the swizzled 128-byte row
+        tc_mma_f16(tmem, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
+                   (kb > 0 || kk > 0) ? 1u : 0u);
+      }
+      tc_commit(&empty[s]);  // stage reusable once these MMAs have read it
+    }
+    tc_commit(done);  // accumulator complete (tracks every MMA issued above)
+  }
+  __syncwarp();
+
+  // ---- epilogue
+  const bool ok = mbar_wait(done, 0);
+  tc_fence_after();
+  if (!ok) atomicExch(&s_fail, 1);
+  __syncthreads();
+  const bool good = (*(volatile int*)&s_fail) == 0;
+  const int r = ti * BM + warp * 32 + lane;
+  const bool diag = (ti == tj);
+  if (good) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      uint32_t v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      tmem_ld_wait();
+      if (r < m) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int c = tj * BN + c0 + j;
+          if (c < m && (!diag || r >= c)) C[(size_t)c * ldc + r] -= __uint_as_float(v[j]);
+        }
+      }
+    }
+  }
+  // ---- teardown: on failure make sure no copy of ours is still landing
+  if (!good && warp == 0 && lane == 0) {
+    for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+      (void)mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1);
+    atomicExch(err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------- host side
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2D map over a row-major rows x cols matrix of 16-bit elements, box 64 x 128.
+static int make_map_16(CUtensorMap* map, const void* base, int rows, int cols, int ld,
+                       CUtensorMapDataType dt) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return JMG_ERR_CUDA;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? JMG_OK : JMG_ERR_CUDA;
+}
+
+int launch_syrk_tc(int m, int kext, const void* PA, const void* PB, int ldp, int prec, float* C,
+                   int ldc, int* err, cudaStream_t s) {
+  if (m <= 0 || kext <= 0) return JMG_OK;
+  if (kext % tc::BK || ldp % 64 || ldp < kext) return JMG_ERR_ALIGN;
+  if ((reinterpret_cast<uintptr_t>(PA) | reinterpret_cast<uintptr_t>(PB)) & 15) return JMG_ERR_ALIGN;
+  if (prec != JMG_PREC_BF16 && prec != JMG_PREC_FP16) return JMG_ERR_UNSUPPORTED;
+  CUtensorMapDataType dt =
+      prec == JMG_PREC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  CUtensorMap ma, mb;
+  JMG_TRY(make_map_16(&ma, PA, m, kext, ldp, dt));
+  JMG_TRY(make_map_16(&mb, PB, m, kext, ldp, dt));
+  static bool attr = false;
+  if (!attr) {
+    JMG_CUDA(cudaFuncSetAttribute(tc::k_syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tc::SMEM_BYTES));
+    attr = true;
+  }
+  long long tiles = tri_tiles(cdiv(m, tc::BM));
+  tc::k_syrk_tc<<<(unsigned)tiles, 128, tc::SMEM_BYTES, s>>>(ma, mb, C, ldc, m, kext,
+                                                              prec == JMG_PREC_BF16 ? 1 : 0, err);
+  return launched();
+}
+
+int launch_syrk_fp8(int, int, const void*, int, const signed char*, float*, int, int*,
+                    cudaStream_t) {
+  return JMG_ERR_UNSUPPORTED;
+}
+
+}  // namespace jmg

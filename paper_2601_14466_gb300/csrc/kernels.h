@@ -1,0 +1,91 @@
+// kernels.h -- internal launchers of the SPD solver's kernels (not exported).
+#pragma once
+
+#include "common.cuh"
+
+namespace jmg {
+
+// Operand access modes of the tiled GEMM:
+//   N: op(A)(i, l) = A[i + l*lda]            (column-major as stored)
+//   T: op(A)(i, l) = A[l + i*lda]            (transposed)
+//   S: op(A)(i, l) = A[max(i,l) + min(i,l)*lda]  (symmetric, lower stored;
+//      i and l are absolute indices of the stored matrix)
+enum Mode { MODE_N = 0, MODE_T = 1, MODE_S = 2 };
+
+// Output of the tiled GEMM:
+//   OUT_SUB:  C[i + j*ldc] -= acc                 (all tiles of the grid)
+//   OUT_SUB_LOWER: same, lower-triangle tiles only and only i >= j written
+//   OUT_PART: part[z][i + j*ldc] = acc            (split-K partial sums)
+enum Out { OUT_SUB = 0, OUT_SUB_LOWER = 1, OUT_PART = 2 };
+
+// ---- factorisation pieces (T = storage type; FP64 arithmetic in potf2)
+int launch_potf2(double* A, int lda, int kb, int koff, int* info, cudaStream_t s);
+int launch_potf2(float* A, int lda, int kb, int koff, int* info, cudaStream_t s);
+
+// A21 (m x kb, in place) <- A21 * Lkk^{-T}; arithmetic in T.
+int launch_trsm(double* A21, int lda, int m, int kb, const double* Lkk, const int* info,
+                cudaStream_t s);
+int launch_trsm(float* A21, int lda, int m, int kb, const float* Lkk, const int* info,
+                cudaStream_t s);
+
+// C (m x n) -= op(A) (m x k) * op(B) (k x n), T arithmetic.
+// For OUT_SUB_LOWER, m == n and the tile grid covers the lower triangle.
+// For OUT_PART, `C` is the partial buffer with `splits` slices of ldc*n.
+template <typename T>
+int launch_gemm(int m, int n, int k, const T* A, int lda, int amode, const T* B, int ldb,
+                int bmode, T* C, int ldc, int out, int splits, const int* info, cudaStream_t s);
+
+// Triangular solve with the diagonal block L (kb x kb) for nrhs columns of B
+// (kb x nrhs, ldb): trans == 0: L Y = B;  trans == 1: L^T X = B.
+template <typename T>
+int launch_trsv_diag(int kb, int nrhs, const T* L, int lda, T* B, int ldb, int trans,
+                     const int* info, cudaStream_t s);
+
+// Blocked solves with the whole factor: L L^T X = B, in place on B.
+template <typename T>
+int blocked_potrs(int n, int nrhs, const T* L, int lda, T* B, int ldb, int nb, const int* info,
+                  cudaStream_t s);
+
+// ---- mixed-precision helpers
+// W (FP32, ldw) <- lower(A) (FP64), lower triangle only; plus shift on the diagonal.
+int launch_lower_to_f32(int n, const double* A, int lda, float* W, int ldw, double shift,
+                        cudaStream_t s);
+// Split FP32 panel L21 (m x kb, ldw) into 16-bit words, written into the
+// extended operands PA / PB (row-major, m x kext, ldp) at K offset `koff`:
+// for each pair p of the pair table, PA[:, p*kb + c] = word a_p, PB = word b_p.
+int launch_split_words(int m, int kb, const float* L21, int ldw, int prec, int words, void* PA,
+                       void* PB, int ldp, cudaStream_t s);
+int split_pairs(int words);  // number of (a, b) word pairs used for `words`
+
+// ---- refinement helpers
+// R = B - A X (A symmetric, lower) in FP64 with split-K partials in `part`
+// (splits * n * nrhs doubles), colmax[0..3 nrhs) = ||r||, ||x||, ||b|| per column.
+int residual_splits(int n, int nrhs);
+int launch_residual(int n, int nrhs, const double* A, int lda, const double* X, int ldx,
+                    const double* B, int ldb, double* R, int ldr, double* colmax, double* part,
+                    int splits, cudaStream_t s);
+// ||A||_inf (lower stored) into *out; rowsum: n doubles of scratch.
+int launch_norm_inf(int n, const double* A, int lda, double* rowsum, double* out,
+                    cudaStream_t s);
+// eta_j = colmax_r / (anorm * colmax_x + colmax_b); eta_out[0] = max_j, eta_out[1..] = eta_j
+int launch_eta(int nrhs, const double* colmax, const double* anorm, double* eta_out,
+               cudaStream_t s);
+// D32[:, j] = fp32(R[:, j] / scale_j), scale_j = colmax_r[j] (1 if zero)
+int launch_scale_to_f32(int n, int nrhs, const double* R, int ldr, const double* colmax_r,
+                        float* D, int ldd, cudaStream_t s);
+// X[:, j] += scale_j * D32[:, j]   (X FP64)
+int launch_axpy_f32(int n, int nrhs, const float* D, int ldd, const double* colmax_r, double* X,
+                    int ldx, cudaStream_t s);
+// copy FP64 -> FP64 column-major blocks
+int launch_copy2d(int n, int nrhs, const double* src, int lds, double* dst, int ldd,
+                  cudaStream_t s);
+// clear n doubles
+int launch_zero(double* p, size_t n, cudaStream_t s);
+
+// ---- tensor-core trailing update (k_tc.cu)
+int launch_syrk_tc(int m, int kext, const void* PA, const void* PB, int ldp, int prec, float* C,
+                   int ldc, int* err, cudaStream_t s);
+int launch_syrk_fp8(int m, int kext, const void* Q, int ldq, const signed char* e, float* C,
+                    int ldc, int* err, cudaStream_t s);
+
+}  // namespace jmg

@@ -1,0 +1,330 @@
+"""Python binding of libjmg.so (ctypes): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; PyTorch supplies
+device memory and the stream.  There is no CPU fallback: if the library is
+missing or no CUDA device is present, the calls raise.
+
+Raw entry points keep the C names (``jmg_potrf``, ``jmg_potrs``, ``jmg_posv``,
+``jmg_workspace_size``, ``jmg_logdet``, ...) and take integers / pointers.  The
+tensor-level helpers (``potrf_``, ``potrs_``, ``posv``, ``logdet``) take torch
+tensors in column-major layout (``stride(0) == 1``): for a symmetric matrix held
+row-major, ``A.mT`` is such a view of the same storage.
+
+Paper: "Software design" -- potrs = Cholesky potrf + potrs (optional log det).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+from . import _build
+
+_lock = threading.Lock()
+_lib = None
+
+JMG_F64, JMG_F32 = 0, 1
+PREC = {"fp64": 0, "native": 0, "bf16": 1, "fp16": 2, "fp8": 3}
+REFINE = {"ir": 0, "pcg": 1, "auto": 2}
+OP_POTRF, OP_POTRS, OP_POSV = 0, 1, 2
+
+STATUS = {0: "ok", 1: "CUDA error", 2: "workspace too small", 3: "matrix is not positive definite",
+          4: "refinement did not reach the tolerance", 5: "device-side wait timed out",
+          6: "unsupported option combination", 7: "alignment requirement not met"}
+
+
+class JmgError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = status
+        msg = STATUS.get(status, "illegal argument %d" % -status if status < 0 else "status %d" % status)
+        super().__init__("%s: %s (status %d)" % (where or "jmg", msg, status))
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("nb", ctypes.c_int), ("NB", ctypes.c_int), ("prec", ctypes.c_int),
+                ("words", ctypes.c_int), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
+                ("refine", ctypes.c_int), ("shift_retry", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("info", ctypes.c_int), ("iters", ctypes.c_int),
+                ("refine_used", ctypes.c_int), ("words_used", ctypes.c_int),
+                ("factor_tries", ctypes.c_int), ("bwd_err", ctypes.c_double),
+                ("shift", ctypes.c_double), ("anorm", ctypes.c_double),
+                ("t_factor_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
+                ("t_refine_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SZ = ctypes.c_size_t
+
+_SIGS = {
+    "jmg_default_options": (None, [ctypes.POINTER(Options)]),
+    "jmg_workspace_size": (_SZ, [_I, _I, _I, _I, ctypes.POINTER(Options)]),
+    "jmg_potrf": (_I, [_I, _P, _I, _I, _P, ctypes.POINTER(Options), _P, _SZ, _P]),
+    "jmg_potrs": (_I, [_I, _I, _P, _I, _P, _I, _I, _P, _SZ, _P]),
+    "jmg_posv": (_I, [_I, _I, _P, _I, _P, _I, _I, _P, ctypes.POINTER(Options),
+                      ctypes.POINTER(Stats), _P, _SZ, _P]),
+    "jmg_logdet": (_I, [_I, _P, _I, _I, _P, _P]),
+    "jmg_status_string": (ctypes.c_char_p, [_I]),
+    "jmg_dev_syrk_tc": (_I, [_I, _I, _P, _P, _I, _I, _P, _I, _P, _P]),
+    "jmg_dev_syrk_fp8": (_I, [_I, _I, _P, _I, _P, _P, _I, _P, _P]),
+    "jmg_dev_residual_workspace": (_SZ, [_I, _I]),
+    "jmg_dev_residual": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P, _SZ, _P]),
+    "jmg_dev_norm_inf": (_I, [_I, _P, _I, _P, _P, _SZ, _P]),
+    "jmg_dev_probe": (_I, [_I, _I, _I, _P, ctypes.POINTER(ctypes.c_double), _P]),
+    "jmg_dev_launch_count": (ctypes.c_longlong, []),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libjmg.so (building it first if it is missing and nvcc exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB) or (build_if_missing and not _build.up_to_date()):
+                if not build_if_missing:
+                    raise RuntimeError("libjmg.so is not built: run __graft_entry__.build()")
+                _build.build()
+            lib = ctypes.CDLL(_build.LIB)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def _chk(st: int, where: str):
+    if st != 0:
+        raise JmgError(st, where)
+
+
+def _stream(dev) -> int:
+    return torch.cuda.current_stream(dev).cuda_stream
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if not t.is_cuda:
+            raise ValueError("jmg: tensors must live on a CUDA device (no CPU path)")
+
+
+def _colmajor(t: torch.Tensor, name: str):
+    if t.dim() != 2:
+        raise ValueError("%s must be 2-D" % name)
+    n, m = t.shape
+    if t.stride(0) != 1 and not (m == 1 and t.is_contiguous()):
+        raise ValueError("%s must be column-major (stride(0) == 1); for a symmetric row-major "
+                         "matrix pass its .mT view" % name)
+    ld = t.stride(1) if m > 1 else max(n, 1)
+    return t.data_ptr(), max(ld, max(n, 1))
+
+
+def colmajor_copy(t: torch.Tensor) -> torch.Tensor:
+    """A column-major copy of a 2-D tensor (stride (1, rows))."""
+    return t.t().contiguous().t() if t.dim() == 2 else t.reshape(-1, 1).clone()
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load().jmg_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if v is None:
+            continue
+        if k == "prec" and isinstance(v, str):
+            v = PREC[v]
+        if k == "refine" and isinstance(v, str):
+            v = REFINE[v]
+        setattr(o, k, v)
+    return o
+
+
+def workspace_size(op: int, n: int, nrhs: int, opts: Options | None = None) -> int:
+    return int(load().jmg_workspace_size(op, n, nrhs, JMG_F64, ctypes.byref(opts) if opts else None))
+
+
+def workspace(op: int, n: int, nrhs: int, opts: Options | None, device) -> torch.Tensor:
+    nbytes = workspace_size(op, n, nrhs, opts)
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+# ------------------------------------------------------------------ tensor helpers
+
+
+def potrf_(A: torch.Tensor, *, nb: int = 128, info: torch.Tensor | None = None) -> torch.Tensor:
+    """Cholesky factorisation in place: lower(A) <- L (FP64, column-major).
+    Returns the device info tensor (int32, 1 element); asynchronous."""
+    _need_cuda(A)
+    if A.dtype != torch.float64:
+        raise TypeError("potrf_: FP64 only")
+    p, lda = _colmajor(A, "A")
+    n = A.shape[0]
+    if info is None:
+        info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    o = default_options(nb=nb)
+    st = load().jmg_potrf(n, p, lda, JMG_F64, info.data_ptr(), ctypes.byref(o), None, 0,
+                          _stream(A.device))
+    _chk(st, "jmg_potrf")
+    return info
+
+
+def potrs_(L: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
+    """Solve (L L^T) X = B in place on B (column-major); asynchronous."""
+    _need_cuda(L, B)
+    pl, lda = _colmajor(L, "L")
+    pb, ldb = _colmajor(B, "B")
+    st = load().jmg_potrs(L.shape[0], B.shape[1], pl, lda, pb, ldb, JMG_F64, None, 0,
+                          _stream(L.device))
+    _chk(st, "jmg_potrs")
+    return B
+
+
+@dataclass
+class SolveInfo:
+    status: int
+    info: int
+    iters: int
+    bwd_err: float
+    shift: float
+    words: int
+    factor_tries: int
+    anorm: float
+    t_factor_ms: float
+    t_solve_ms: float
+    t_refine_ms: float
+    refine_used: int
+
+
+def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1, nb: int = 128,
+         tol: float = 1e-13, maxit: int = 30, refine: str = "auto", shift_retry: bool = True,
+         overwrite_a: bool = False, work: torch.Tensor | None = None, check: bool = True):
+    """Solve A X = B for SPD A (lower triangle of the column-major A read).
+
+    prec "fp64": potrf + potrs in FP64 (A is overwritten with L only when
+    ``overwrite_a``; otherwise a copy is factored).  prec "bf16"/"fp16": mixed
+    precision with tensor-core trailing updates and FP64 refinement; A is
+    preserved.  Returns ``(X, SolveInfo)``; X is a new column-major tensor."""
+    _need_cuda(A, B)
+    if A.dtype != torch.float64 or B.dtype != torch.float64:
+        raise TypeError("posv: FP64 storage only")
+    squeeze = B.dim() == 1
+    if squeeze:
+        B = B.reshape(-1, 1)
+    n, nrhs = A.shape[0], B.shape[1]
+    X = colmajor_copy(B)
+    o = default_options(nb=nb, prec=prec, words=words, tol=tol, maxit=maxit, refine=refine,
+                        shift_retry=int(shift_retry))
+    Aw = A if (overwrite_a or o.prec != 0) else colmajor_copy(A)
+    pa, lda = _colmajor(Aw, "A")
+    px, ldx = _colmajor(X, "B")
+    info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    stats = Stats()
+    if work is None and o.prec != 0:
+        work = workspace(OP_POSV, n, nrhs, o, A.device)
+    wp, wl = (work.data_ptr(), work.numel()) if work is not None else (None, 0)
+    st = load().jmg_posv(n, nrhs, pa, lda, px, ldx, JMG_F64, info.data_ptr(), ctypes.byref(o),
+                         ctypes.byref(stats), wp, wl, _stream(A.device))
+    if o.prec == 0:
+        info_h = int(info.item()) if check else 0
+        si = SolveInfo(st, info_h, 0, float("nan"), 0.0, 0, 1, float("nan"), 0, 0, 0, -1)
+        if check and (st != 0 or info_h != 0):
+            raise JmgError(st if st else 3, "jmg_posv(info=%d)" % info_h)
+    else:
+        si = SolveInfo(stats.status, stats.info, stats.iters, stats.bwd_err, stats.shift,
+                       stats.words_used, stats.factor_tries, stats.anorm, stats.t_factor_ms,
+                       stats.t_solve_ms, stats.t_refine_ms, stats.refine_used)
+        if check and st != 0:
+            raise JmgError(st, "jmg_posv")
+    return (X[:, 0] if squeeze else X), si
+
+
+def logdet(L: torch.Tensor) -> torch.Tensor:
+    """log det A = 2 sum log L_ii from a factor made by potrf_ (device scalar)."""
+    _need_cuda(L)
+    pl, lda = _colmajor(L, "L")
+    out = torch.empty((), dtype=torch.float64, device=L.device)
+    _chk(load().jmg_logdet(L.shape[0], pl, lda, JMG_F64, out.data_ptr(), _stream(L.device)),
+         "jmg_logdet")
+    return out
+
+
+def residual(A: torch.Tensor, X: torch.Tensor, B: torch.Tensor):
+    """FP64 R = B - A X (lower(A) read) and per-column norms (r, x, b)."""
+    _need_cuda(A, X, B)
+    n, nrhs = X.shape
+    pa, lda = _colmajor(A, "A")
+    px, ldx = _colmajor(X, "X")
+    pb, ldb = _colmajor(B, "B")
+    R = torch.empty((nrhs, n), dtype=torch.float64, device=A.device).t()
+    colmax = torch.zeros(3 * nrhs, dtype=torch.float64, device=A.device)
+    lw = int(load().jmg_dev_residual_workspace(n, nrhs))
+    work = torch.empty(max(lw, 8), dtype=torch.uint8, device=A.device)
+    st = load().jmg_dev_residual(n, nrhs, pa, lda, px, ldx, pb, ldb, R.data_ptr(), n,
+                                 colmax.data_ptr(), work.data_ptr(), lw, _stream(A.device))
+    _chk(st, "jmg_dev_residual")
+    return R, colmax.view(3, nrhs)
+
+
+def norm_inf(A: torch.Tensor) -> torch.Tensor:
+    _need_cuda(A)
+    pa, lda = _colmajor(A, "A")
+    n = A.shape[0]
+    out = torch.empty((), dtype=torch.float64, device=A.device)
+    work = torch.empty(max(n, 1), dtype=torch.float64, device=A.device)
+    st = load().jmg_dev_norm_inf(n, pa, lda, out.data_ptr(), work.data_ptr(), work.numel() * 8,
+                                 _stream(A.device))
+    _chk(st, "jmg_dev_norm_inf")
+    return out
+
+
+def syrk_tc_(C: torch.Tensor, PA: torch.Tensor, PB: torch.Tensor | None = None) -> torch.Tensor:
+    """C_lower -= PA PB^T on the tensor cores.  PA, PB: m x kext row-major
+    bfloat16 or float16 (kext multiple of 64); C: FP32 column-major."""
+    _need_cuda(C, PA)
+    PB = PA if PB is None else PB
+    if PA.dtype not in (torch.bfloat16, torch.float16) or PB.dtype != PA.dtype:
+        raise TypeError("syrk_tc_: PA/PB must be bf16 or fp16 of one type")
+    if not (PA.is_contiguous() and PB.is_contiguous()):
+        raise ValueError("syrk_tc_: PA/PB must be row-major contiguous")
+    m, kext = PA.shape
+    pc, ldc = _colmajor(C, "C")
+    err = torch.zeros(1, dtype=torch.int32, device=C.device)
+    prec = PREC["bf16"] if PA.dtype == torch.bfloat16 else PREC["fp16"]
+    st = load().jmg_dev_syrk_tc(m, kext, PA.data_ptr(), PB.data_ptr(), kext, prec, pc, ldc,
+                                err.data_ptr(), _stream(C.device))
+    _chk(st, "jmg_dev_syrk_tc")
+    return err
+
+
+def probe(kind: int, blocks: int, iters: int, device="cuda"):
+    """Launch one throughput probe; returns (flops, elapsed_ms)."""
+    sink = torch.zeros(max(blocks, 1), dtype=torch.float64, device=device)
+    flops = ctypes.c_double(0)
+    s = torch.cuda.current_stream(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    _chk(load().jmg_dev_probe(kind, blocks, iters, sink.data_ptr(), ctypes.byref(flops),
+                              s.cuda_stream), "jmg_dev_probe")
+    e1.record(s)
+    e1.synchronize()
+    return flops.value, e0.elapsed_time(e1)
+
+
+def launch_count() -> int:
+    return int(load().jmg_dev_launch_count())

@@ -1,0 +1,87 @@
+"""CPU-only checks of the C ABI: the library builds and loads, exports every
+symbol that include/*.h declares, and rejects illegal arguments (LAPACK-style
+negative codes) before touching the GPU."""
+from __future__ import annotations
+
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2601_14466_gb300 import jmg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(jmg_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_headers_declare_the_core_calls():
+    d = declared_symbols()
+    for name in ("jmg_potrf", "jmg_potrs", "jmg_posv", "jmg_workspace_size", "jmg_logdet"):
+        assert name in d
+
+
+def test_library_exports_every_declared_symbol():
+    lib = jmg.load()
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+    # and the binding wires every one of them
+    assert set(declared_symbols()) <= set(jmg.exported_symbols())
+
+
+def test_illegal_arguments_are_rejected_on_the_host():
+    lib = jmg.load()
+    info = ctypes.c_void_p(1)  # never dereferenced: the checks fire first
+    assert lib.jmg_potrf(-1, None, 1, 0, info, None, None, 0, None) == -1
+    assert lib.jmg_potrf(10, None, 5, 0, info, None, None, 0, None) == -3
+    assert lib.jmg_potrf(10, None, 10, 9, info, None, None, 0, None) == -4
+    assert lib.jmg_potrf(10, None, 10, 0, None, None, None, 0, None) == -5
+    assert lib.jmg_potrs(-1, 1, None, 1, None, 1, 0, None, 0, None) == -1
+    assert lib.jmg_potrs(4, -1, None, 4, None, 4, 0, None, 0, None) == -2
+    assert lib.jmg_potrs(4, 1, None, 3, None, 4, 0, None, 0, None) == -4
+    assert lib.jmg_potrs(4, 1, None, 4, None, 3, 0, None, 0, None) == -6
+    assert lib.jmg_potrs(0, 0, None, 1, None, 1, 0, None, 0, None) == 0
+    assert lib.jmg_posv(-2, 1, None, 1, None, 1, 0, info, None, None, None, 0, None) == -1
+    assert lib.jmg_posv(4, 1, None, 4, None, 4, 0, None, None, None, None, 0, None) == -8
+    o = jmg.default_options(nb=100)
+    assert lib.jmg_posv(4, 1, None, 4, None, 4, 0, info, ctypes.byref(o), None, None, 0,
+                        None) == -9
+    # mixed posv without workspace
+    o = jmg.default_options(prec="bf16")
+    assert lib.jmg_posv(256, 2, ctypes.c_void_p(256), 256, ctypes.c_void_p(512), 256, 0, info,
+                        ctypes.byref(o), None, None, 0, None) == 2  # JMG_ERR_WORKSPACE
+
+
+def test_defaults_and_workspace():
+    o = jmg.default_options()
+    assert (o.nb, o.prec, o.words, o.maxit) == (128, 0, 1, 30)
+    assert abs(o.tol - 1e-13) < 1e-30
+    assert jmg.workspace_size(jmg.OP_POTRF, 1000, 1, o) == 0
+    assert jmg.workspace_size(jmg.OP_POSV, 1000, 4, o) == 0
+    om = jmg.default_options(prec="bf16")
+    w1 = jmg.workspace_size(jmg.OP_POSV, 1000, 4, om)
+    w2 = jmg.workspace_size(jmg.OP_POSV, 2000, 4, om)
+    assert 4 * 1000 * 1000 <= w1 < w2
+    om3 = jmg.default_options(prec="bf16", words=3)
+    assert jmg.workspace_size(jmg.OP_POSV, 1000, 4, om3) > w1
+    assert jmg.load().jmg_status_string(3) == b"matrix is not positive definite"
+
+
+def test_no_cpu_fallback():
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("checks the CPU-only refusal")
+    A = torch.eye(4, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        jmg.posv(A, torch.ones(4, 1, dtype=torch.float64))

@@ -1,0 +1,70 @@
+"""Mixed-precision posv (tensor-core factor + FP64 refinement) against the
+oracle: backward error certified by the oracle's Dot2 residual, solution
+compared with the oracle's FP64 solve within a kappa-scaled bound, and A left
+untouched.  Paper: "Software design" (potrs semantics)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2601_14466_gb300 import inputs, jmg
+from tests.helpers import U64, host, lower_only, to_dev_colmajor
+
+pytestmark = pytest.mark.gpu
+
+
+def _check(A, B, X, kappa, tol=1e-13):
+    Xg = host(X)
+    eta, _ = oracle.bwd_err(A.numpy(), Xg, B.numpy())
+    assert eta <= tol, eta
+    Xo, io = oracle.posv(A.numpy(), B.numpy())
+    assert io == 0
+    # both solutions have backward error <= tol: they differ by <= ~2 kappa tol
+    bound = 4 * kappa * max(tol, U64) * np.abs(Xo).max() * 10
+    assert np.abs(Xg - Xo).max() <= bound
+    return eta
+
+
+@pytest.mark.parametrize("prec,words", [("bf16", 1), ("bf16", 2), ("bf16", 3), ("fp16", 1),
+                                        ("fp16", 2)])
+@pytest.mark.parametrize("n,nrhs", [(130, 1), (700, 4), (1100, 16)])
+def test_posv_mixed_gram(prec, words, n, nrhs):
+    A = inputs.gram_shift(n, 1.0, seed=inputs.seed_for("mixed", n))
+    Xt = inputs.uniform(n, nrhs, seed=5)
+    B = inputs.rhs_from(A, Xt)
+    Ad, _ = to_dev_colmajor(lower_only(A))
+    A_before = Ad.clone()
+    Bd, _ = to_dev_colmajor(B)
+    X, si = jmg.posv(Ad, Bd, prec=prec, words=words)
+    assert si.status == 0 and si.info == 0
+    assert si.bwd_err <= 1e-13
+    _check(A, B, X, kappa=10.0)
+    # A is preserved bit for bit (NaN canary in the upper triangle included)
+    assert torch.equal(torch.nan_to_num(Ad, nan=7.0), torch.nan_to_num(A_before, nan=7.0))
+
+
+@pytest.mark.parametrize("kappa,prec,words", [(1e2, "bf16", 1), (1e4, "bf16", 2),
+                                              (1e4, "fp16", 1), (1e6, "bf16", 3)])
+def test_posv_mixed_q_lambda(kappa, prec, words):
+    n, nrhs = 1000, 4
+    A = inputs.q_lambda(n, kappa, seed=inputs.seed_for("qlam", kappa))
+    Xt = inputs.uniform(n, nrhs, seed=6)
+    B = inputs.rhs_from(A, Xt)
+    Ad, _ = to_dev_colmajor(lower_only(A))
+    Bd, _ = to_dev_colmajor(B)
+    X, si = jmg.posv(Ad, Bd, prec=prec, words=words, maxit=60)
+    assert si.status == 0, si
+    _check(A, B, X, kappa)
+
+
+def test_posv_mixed_not_spd():
+    n = 300
+    A = inputs.gram_shift(n, 1.0, seed=2)
+    A[100, 100] = -50.0
+    Ad, _ = to_dev_colmajor(A)
+    Bd, _ = to_dev_colmajor(inputs.uniform(n, 1, seed=1))
+    X, si = jmg.posv(Ad, Bd, prec="bf16", shift_retry=False, check=False)
+    assert si.status == 3  # JMG_ERR_NOT_SPD
+    assert si.info == 101
