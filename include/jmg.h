@@ -69,6 +69,7 @@ typedef struct {
   int maxit;        /* maximum refinement iterations                                */
   int refine;       /* jmg_refine                                                   */
   int shift_retry;  /* low-precision breakdown: retry with a diagonal shift (0/1)   */
+  int timing;       /* 1: time the FP64 residual kernel with CUDA events (stats)    */
 } jmg_options;
 
 /* Host-side report of one posv call (filled when the call returns). */
@@ -83,10 +84,12 @@ typedef struct {
   double shift;     /* diagonal shift of the factor (0 if none)                     */
   double anorm;     /* ||A||_inf                                                     */
   double t_factor_ms, t_solve_ms, t_refine_ms; /* host-timed phases (0 if not synced) */
+  double t_resid_gpu_ms; /* with opt->timing: summed CUDA-event time of the residual GEMM */
+  int n_resid;           /* number of residual evaluations                            */
 } jmg_stats;
 
 /* Fill *opt with the defaults: nb 128, NB 128, prec NATIVE, words 1, tol 1e-13,
- * maxit 30, refine AUTO, shift_retry 1. */
+ * maxit 30, refine AUTO, shift_retry 1, timing 0. */
 void jmg_default_options(jmg_options* opt);
 
 /* Bytes of `work` that the call (op, n, nrhs, dtype, opt) needs; 0 is valid. */

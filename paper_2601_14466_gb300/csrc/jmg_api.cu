@@ -223,10 +223,22 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
   double prev = INFINITY;
   int stall = 0;
   int it = 0;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (o.timing) {
+    JMG_CUDA(cudaEventCreate(&ev[0]));
+    JMG_CUDA(cudaEventCreate(&ev[1]));
+  }
   for (;; ++it) {
-    JMG_TRY(launch_residual(n, nrhs, A, lda, X, n, B, ldb, R, n, colmax, part, p.splits, s));
+    JMG_TRY(launch_residual(n, nrhs, A, lda, X, n, B, ldb, R, n, colmax, part, p.splits, s, ev[0],
+                            ev[1]));
     JMG_TRY(launch_eta(nrhs, colmax, anorm, eta, s));
     JMG_TRY(sync_read(eh.data(), eta, sizeof(double) * (1 + nrhs), s));
+    S.n_resid++;
+    if (o.timing) {
+      float ms = 0.f;
+      JMG_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+      S.t_resid_gpu_ms += ms;
+    }
     S.bwd_err = eh[0];
     if (eh[0] <= o.tol) break;
     if (it >= o.maxit || std::isnan(eh[0])) {
@@ -242,6 +254,10 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
     JMG_TRY(precond_update(n, nrhs, W, p.ldw, R, colmax, D, X, o.nb, s));
   }
   S.iters = it;
+  if (o.timing) {
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+  }
   JMG_TRY(launch_copy2d(n, nrhs, X, n, B, ldb, s));
   JMG_CUDA(cudaStreamSynchronize(s));
   double t3 = now_ms();
@@ -273,6 +289,7 @@ void jmg_default_options(jmg_options* o) {
   o->maxit = 30;
   o->refine = JMG_REFINE_AUTO;
   o->shift_retry = 1;
+  o->timing = 0;
 }
 
 size_t jmg_workspace_size(int op, int n, int nrhs, int dtype, const jmg_options* opt) {

@@ -15,15 +15,21 @@ long long g_launches = 0;
 // ============================================================================
 // potf2: Cholesky of one diagonal block (kb <= NBMAX) in shared memory, FP64.
 // Storage type T (double: plain path; float: the FP32 working matrix of the
-// mixed path).  Right-looking within the block: pivot, scale the column,
-// rank-1 update of the remaining lower triangle.  On a pivot that is not > 0
-// (or NaN) it records info = koff + j + 1 and stops; the partly factored
-// block is written back, as LAPACK does.
+// mixed path).  Right-looking within the block with ONE barrier per column:
+//   - column j's pivot l_jj = sqrt(d_j) and 1/l_jj were computed before the
+//     barrier by the thread that applied the last update to d_j;
+//   - every thread (row r, column group g) writes l_rj = a_rj / l_jj straight
+//     to global memory and applies a_rc -= (a_rj / d_j) * a_cj, which equals
+//     l_rj * l_cj, for its columns c in (j, r] -- column j itself is only read;
+//   - the thread owning row j+1 then finishes d_{j+1} and its pivot.
+// A pivot that is not > 0 (or NaN) records info = koff + j + 1 and stops;
+// the columns before it are final, the rest keep their input values.
 // ============================================================================
 template <typename T, int NBMAX>
 __global__ void __launch_bounds__(256) k_potf2(T* __restrict__ A, int lda, int kb, int koff,
                                                int* __restrict__ info) {
   extern __shared__ double sm_potf2[];
+  __shared__ double s_ljj[NBMAX], s_inv[NBMAX];
   __shared__ int fail;
   if (*(volatile int*)info != 0) return;  // an earlier block already failed
   const int ld = kb + 1;
@@ -33,32 +39,45 @@ __global__ void __launch_bounds__(256) k_potf2(T* __restrict__ A, int lda, int k
     int i = idx % kb, j = idx / kb;
     if (i >= j) s[j * ld + i] = (double)A[(size_t)j * lda + i];
   }
-  if (t == 0) fail = 0;
+  __syncthreads();
+  if (t == 0) {
+    fail = 0;
+    const double d = s[0];
+    if (!(d > 0.0)) {
+      fail = 1;
+    } else {
+      const double l = sqrt(d);
+      s_ljj[0] = l;
+      s_inv[0] = 1.0 / l;
+    }
+  }
   __syncthreads();
   constexpr int G = 256 / NBMAX;  // column groups
   const int r = t % NBMAX, g = t / NBMAX;
   for (int j = 0; j < kb; ++j) {
-    if (t == 0) {
-      double d = s[j * ld + j];
-      if (!(d > 0.0))
-        fail = j + 1;
-      else
-        s[j * ld + j] = sqrt(d);
-    }
-    __syncthreads();
     if (fail) break;
-    const double ljj = s[j * ld + j];
-    if (g == 0 && r > j && r < kb) s[j * ld + r] = s[j * ld + r] / ljj;
-    __syncthreads();
-    if (r > j && r < kb) {
-      const double lrj = s[j * ld + r];
-      for (int c = j + 1 + g; c <= r; c += G) s[c * ld + r] -= lrj * s[j * ld + c];
+    if (r >= j && r < kb) {
+      const double inv = s_inv[j];
+      const double arj = s[j * ld + r];
+      const double lrj = (r == j) ? s_ljj[j] : arj * inv;
+      if (g == 0) A[(size_t)j * lda + r] = (T)lrj;
+      if (r > j) {
+        const double q = lrj * inv;  // a_rj / d_j
+#pragma unroll 4
+        for (int c = j + 1 + g; c <= r; c += G) s[c * ld + r] -= q * s[j * ld + c];
+        if (g == 0 && r == j + 1) {  // this thread applied the last update to d_{j+1}
+          const double d = s[r * ld + r];
+          if (!(d > 0.0)) {
+            fail = r + 1;
+          } else {
+            const double l = sqrt(d);
+            s_ljj[r] = l;
+            s_inv[r] = 1.0 / l;
+          }
+        }
+      }
     }
     __syncthreads();
-  }
-  for (int idx = t; idx < kb * kb; idx += blockDim.x) {
-    int i = idx % kb, j = idx / kb;
-    if (i >= j) A[(size_t)j * lda + i] = (T)s[j * ld + i];
   }
   if (t == 0 && fail) atomicCAS(info, 0, koff + fail);
 }
@@ -473,11 +492,13 @@ __global__ void k_resid_reduce(int n, int nrhs, int splits, const double* __rest
 
 int launch_residual(int n, int nrhs, const double* A, int lda, const double* X, int ldx,
                     const double* B, int ldb, double* R, int ldr, double* colmax, double* part,
-                    int splits, cudaStream_t s) {
+                    int splits, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
   if (n <= 0 || nrhs <= 0) return JMG_OK;
   JMG_CUDA(cudaMemsetAsync(colmax, 0, sizeof(double) * 3 * nrhs, s));
+  if (ev0) JMG_CUDA(cudaEventRecord(ev0, s));
   JMG_TRY(launch_gemm<double>(n, nrhs, n, A, lda, MODE_S, X, ldx, MODE_N, part, n, OUT_PART, splits,
                               nullptr, s));
+  if (ev1) JMG_CUDA(cudaEventRecord(ev1, s));
   // number of splits actually used by the GEMM grid
   int kchunk = (int)round_up((size_t)cdiv(n, splits), GBK);
   int used = cdiv(n, kchunk);

@@ -63,7 +63,8 @@ int split_pairs(int words);  // number of (a, b) word pairs used for `words`
 int residual_splits(int n, int nrhs);
 int launch_residual(int n, int nrhs, const double* A, int lda, const double* X, int ldx,
                     const double* B, int ldb, double* R, int ldr, double* colmax, double* part,
-                    int splits, cudaStream_t s);
+                    int splits, cudaStream_t s, cudaEvent_t ev0 = nullptr,
+                    cudaEvent_t ev1 = nullptr);
 // ||A||_inf (lower stored) into *out; rowsum: n doubles of scratch.
 int launch_norm_inf(int n, const double* A, int lda, double* rowsum, double* out,
                     cudaStream_t s);

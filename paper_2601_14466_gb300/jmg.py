@@ -46,7 +46,7 @@ class JmgError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int), ("NB", ctypes.c_int), ("prec", ctypes.c_int),
                 ("words", ctypes.c_int), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
-                ("refine", ctypes.c_int), ("shift_retry", ctypes.c_int)]
+                ("refine", ctypes.c_int), ("shift_retry", ctypes.c_int), ("timing", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -55,7 +55,8 @@ class Stats(ctypes.Structure):
                 ("factor_tries", ctypes.c_int), ("bwd_err", ctypes.c_double),
                 ("shift", ctypes.c_double), ("anorm", ctypes.c_double),
                 ("t_factor_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
-                ("t_refine_ms", ctypes.c_double)]
+                ("t_refine_ms", ctypes.c_double), ("t_resid_gpu_ms", ctypes.c_double),
+                ("n_resid", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -137,8 +138,12 @@ def _colmajor(t: torch.Tensor, name: str):
 
 
 def colmajor_copy(t: torch.Tensor) -> torch.Tensor:
-    """A column-major copy of a 2-D tensor (stride (1, rows))."""
-    return t.t().contiguous().t() if t.dim() == 2 else t.reshape(-1, 1).clone()
+    """A NEW column-major copy of a 2-D tensor (stride (1, rows)); never an alias."""
+    if t.dim() != 2:
+        t = t.reshape(-1, 1)
+    out = torch.empty((t.shape[1], t.shape[0]), dtype=t.dtype, device=t.device).t()
+    out.copy_(t)
+    return out
 
 
 def default_options(**kw) -> Options:
@@ -209,11 +214,14 @@ class SolveInfo:
     t_solve_ms: float
     t_refine_ms: float
     refine_used: int
+    t_resid_gpu_ms: float = 0.0
+    n_resid: int = 0
 
 
 def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1, nb: int = 128,
          tol: float = 1e-13, maxit: int = 30, refine: str = "auto", shift_retry: bool = True,
-         overwrite_a: bool = False, work: torch.Tensor | None = None, check: bool = True):
+         overwrite_a: bool = False, work: torch.Tensor | None = None, check: bool = True,
+         timing: bool = False):
     """Solve A X = B for SPD A (lower triangle of the column-major A read).
 
     prec "fp64": potrf + potrs in FP64 (A is overwritten with L only when
@@ -229,7 +237,7 @@ def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1
     n, nrhs = A.shape[0], B.shape[1]
     X = colmajor_copy(B)
     o = default_options(nb=nb, prec=prec, words=words, tol=tol, maxit=maxit, refine=refine,
-                        shift_retry=int(shift_retry))
+                        shift_retry=int(shift_retry), timing=int(timing))
     Aw = A if (overwrite_a or o.prec != 0) else colmajor_copy(A)
     pa, lda = _colmajor(Aw, "A")
     px, ldx = _colmajor(X, "B")
@@ -248,7 +256,8 @@ def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1
     else:
         si = SolveInfo(stats.status, stats.info, stats.iters, stats.bwd_err, stats.shift,
                        stats.words_used, stats.factor_tries, stats.anorm, stats.t_factor_ms,
-                       stats.t_solve_ms, stats.t_refine_ms, stats.refine_used)
+                       stats.t_solve_ms, stats.t_refine_ms, stats.refine_used,
+                       stats.t_resid_gpu_ms, stats.n_resid)
         if check and st != 0:
             raise JmgError(st, "jmg_posv")
     return (X[:, 0] if squeeze else X), si

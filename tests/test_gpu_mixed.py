@@ -59,6 +59,23 @@ def test_posv_mixed_q_lambda(kappa, prec, words):
     _check(A, B, X, kappa)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+def test_posv_leaves_inputs_alone(prec):
+    # posv returns a new X: neither B nor (without overwrite_a) A may change,
+    # also when they are already column-major
+    n, nrhs = 300, 5
+    A = inputs.gram_shift(n, 1.0, seed=12)
+    B = inputs.uniform(n, nrhs, seed=13)
+    Ad, _ = to_dev_colmajor(A)
+    Bd, _ = to_dev_colmajor(B)
+    A0, B0 = Ad.clone(), Bd.clone()
+    X, _ = jmg.posv(Ad, Bd, prec=prec)
+    X2, _ = jmg.posv(Ad, Bd, prec=prec)
+    assert torch.equal(Ad, A0) and torch.equal(Bd, B0)
+    assert X.data_ptr() != Bd.data_ptr()
+    assert torch.allclose(X, X2, rtol=1e-12, atol=0)
+
+
 def test_posv_mixed_not_spd():
     n = 300
     A = inputs.gram_shift(n, 1.0, seed=2)
