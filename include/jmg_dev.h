@@ -16,16 +16,17 @@ extern "C" {
 /*
  * Trailing-matrix update on the tensor cores (the SYRK step of a right-looking
  * blocked Cholesky factorisation):
- *     C[i, j] -= sum_k PA[i, k] * PB[j, k]     for 0 <= j <= i < m
+ *     C[i, j] -= sum_k PA[i, k] * PB[j, k]     for 0 <= j <= i < m, j < ncols
  * PA, PB: m x kext, ROW-major (k contiguous), leading dimension ldp elements,
  *   element type BF16 (prec JMG_PREC_BF16) or FP16 (JMG_PREC_FP16); kext and
  *   ldp multiples of 64; base addresses 16-byte aligned.  PB may equal PA.
- * C: FP32, column-major, ldc >= m; the strict upper triangle is not touched.
+ * C: FP32, column-major, ldc >= m; only the lower trapezoid (rows >= columns,
+ *   columns < ncols <= m) is touched.
  * err: device int; set non-zero if a device-side wait ran out (the update is
  *   then incomplete).  Asynchronous.
  */
-int jmg_dev_syrk_tc(int m, int kext, const void* PA, const void* PB, int ldp, int prec,
-                    float* C, int ldc, int* err, void* stream);
+int jmg_dev_syrk_tc(int m, int ncols, int kext, const void* PA, const void* PB, int ldp,
+                    int prec, float* C, int ldc, int* err, void* stream);
 
 /*
  * FP8 (e4m3) variant with one power-of-two scale per 128 x 128 tile:

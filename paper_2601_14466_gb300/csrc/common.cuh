@@ -50,6 +50,8 @@ JMG_DEV void tri_index(int b, int& ti, int& tj) {
   tj = b - t * (t + 1) / 2;
 }
 
+JMG_DEV int cdiv_dev(int a, int b) { return (a + b - 1) / b; }
+
 JMG_DEV uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

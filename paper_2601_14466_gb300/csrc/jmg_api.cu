@@ -25,7 +25,7 @@ namespace jmg {
 struct Plan {
   size_t off_W = 0, off_PA = 0, off_PB = 0, off_X = 0, off_R = 0, off_D = 0, off_part = 0,
          off_colmax = 0, off_eta = 0, off_anorm = 0, off_rowsum = 0, off_ints = 0, off_Z = 0,
-         off_P = 0, off_Q = 0, off_scal = 0, total = 0;
+         off_P = 0, off_Q = 0, off_scal = 0, off_sync = 0, total = 0;
   int ldw = 0, ldp = 0, kext = 0, splits = 1;
 };
 
@@ -71,8 +71,15 @@ static Plan plan_posv_mixed(int n, int nrhs, const jmg_options& o) {
   p.off_P = take(sizeof(double) * N * R);
   p.off_Q = take(sizeof(double) * N * R);
   p.off_scal = take(sizeof(double) * 8 * R);
+  p.off_sync = take(sizeof(int) * trsv_sync_ints(n, nrhs > 0 ? nrhs : 1));
   p.total = off;
   return p;
+}
+
+// scratch of the plain potrs / posv: the solve's tickets and flags only
+static size_t plain_solve_bytes(int n, int nrhs) {
+  if (n <= 0 || nrhs <= 0) return 0;
+  return round_up(sizeof(int) * trsv_sync_ints(n, nrhs), 256);
 }
 
 template <typename T>
@@ -114,7 +121,7 @@ static int factor_mixed(int n, float* W, int ldw, const jmg_options& o, const Pl
     float* L21 = Wkk + kb;
     JMG_TRY(launch_trsm(L21, ldw, m, kb, Wkk, info_f, s));
     JMG_TRY(launch_split_words(m, kb, L21, ldw, o.prec, o.words, PA, PB, p.ldp, s));
-    JMG_TRY(launch_syrk_tc(m, kb * split_pairs(o.words), PA, PB, p.ldp, o.prec,
+    JMG_TRY(launch_syrk_tc(m, m, kb * split_pairs(o.words), PA, PB, p.ldp, o.prec,
                            W + (size_t)(k + kb) * ldw + (k + kb), ldw, err, s));
   }
   return JMG_OK;
@@ -150,9 +157,10 @@ static int sync_read(void* host, const void* dev, size_t bytes, cudaStream_t s) 
 
 // M^{-1} R in FP32 with per-column scaling, added to X (FP64): X += s * (L L^T)^{-1} (R / s)
 static int precond_update(int n, int nrhs, const float* W, int ldw, const double* R,
-                          const double* colmax_r, float* D, double* X, int nb, cudaStream_t s) {
+                          const double* colmax_r, float* D, double* X, int* sync,
+                          cudaStream_t s) {
   JMG_TRY(launch_scale_to_f32(n, nrhs, R, n, colmax_r, D, n, s));
-  JMG_TRY(blocked_potrs<float>(n, nrhs, W, ldw, D, n, nb, nullptr, s));
+  JMG_TRY(solve_llt<float>(n, nrhs, W, ldw, D, n, sync, nullptr, s));
   JMG_TRY(launch_axpy_f32(n, nrhs, D, n, colmax_r, X, n, s));
   return JMG_OK;
 }
@@ -215,7 +223,7 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
     k_copy_colmax<<<grid, 256, 0, s>>>(n, B, ldb, R, colmax);
     JMG_TRY(launched());
   }
-  JMG_TRY(precond_update(n, nrhs, W, p.ldw, R, colmax, D, X, o.nb, s));
+  JMG_TRY(precond_update(n, nrhs, W, p.ldw, R, colmax, D, X, at<int>(work, p.off_sync), s));
   double t2 = now_ms();
 
   // FP64 iterative refinement
@@ -251,7 +259,7 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
       break;
     }
     prev = eh[0];
-    JMG_TRY(precond_update(n, nrhs, W, p.ldw, R, colmax, D, X, o.nb, s));
+    JMG_TRY(precond_update(n, nrhs, W, p.ldw, R, colmax, D, X, at<int>(work, p.off_sync), s));
   }
   S.iters = it;
   if (o.timing) {
@@ -298,6 +306,7 @@ size_t jmg_workspace_size(int op, int n, int nrhs, int dtype, const jmg_options*
   opts_or_default(opt, &o);
   if (op == JMG_OP_POSV && o.prec != JMG_PREC_NATIVE && n > 0)
     return plan_posv_mixed(n, nrhs, o).total;
+  if (op == JMG_OP_POSV || op == JMG_OP_POTRS) return plain_solve_bytes(n, nrhs);
   return 0;
 }
 
@@ -333,8 +342,6 @@ int jmg_potrf(int n, void* A, int lda, int dtype, int* info, const jmg_options* 
 
 int jmg_potrs(int n, int nrhs, const void* L, int lda, void* B, int ldb, int dtype, void* work,
               size_t lwork, void* stream) {
-  (void)work;
-  (void)lwork;
   if (n < 0) return -1;
   if (nrhs < 0) return -2;
   if (lda < std::max(1, n)) return -4;
@@ -343,8 +350,10 @@ int jmg_potrs(int n, int nrhs, const void* L, int lda, void* B, int ldb, int dty
   if (n == 0 || nrhs == 0) return JMG_OK;
   if (!L) return -3;
   if (!B) return -5;
-  return blocked_potrs<double>(n, nrhs, (const double*)L, lda, (double*)B, ldb, 128, nullptr,
-                               (cudaStream_t)stream);
+  if (!work || lwork < plain_solve_bytes(n, nrhs)) return JMG_ERR_WORKSPACE;
+  if (reinterpret_cast<uintptr_t>(work) & 15) return JMG_ERR_ALIGN;
+  return solve_llt<double>(n, nrhs, (const double*)L, lda, (double*)B, ldb, (int*)work, nullptr,
+                           (cudaStream_t)stream);
 }
 
 int jmg_posv(int n, int nrhs, void* A, int lda, void* B, int ldb, int dtype, int* info,
@@ -367,11 +376,13 @@ int jmg_posv(int n, int nrhs, void* A, int lda, void* B, int ldb, int dtype, int
   if (!A) return -3;
   if (nrhs > 0 && !B) return -5;
   if (o.prec == JMG_PREC_NATIVE) {
+    if (nrhs > 0 && (!work || lwork < plain_solve_bytes(n, nrhs))) return JMG_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(work) & 15) return JMG_ERR_ALIGN;
     JMG_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
     JMG_TRY(potrf_f64(n, (double*)A, lda, o.nb, info, s));
     if (nrhs > 0)
-      JMG_TRY(blocked_potrs<double>(n, nrhs, (const double*)A, lda, (double*)B, ldb, o.nb, info,
-                                    s));
+      JMG_TRY(solve_llt<double>(n, nrhs, (const double*)A, lda, (double*)B, ldb, (int*)work, info,
+                                s));
     return JMG_OK;
   }
   if (o.prec != JMG_PREC_BF16 && o.prec != JMG_PREC_FP16) return JMG_ERR_UNSUPPORTED;
@@ -407,12 +418,13 @@ int jmg_logdet(int n, const void* L, int lda, int dtype, double* out, void* stre
 }
 
 // ---------------------------------------------------------------- dev entry points
-int jmg_dev_syrk_tc(int m, int kext, const void* PA, const void* PB, int ldp, int prec, float* C,
-                    int ldc, int* err, void* stream) {
+int jmg_dev_syrk_tc(int m, int ncols, int kext, const void* PA, const void* PB, int ldp,
+                    int prec, float* C, int ldc, int* err, void* stream) {
   if (m < 0) return -1;
-  if (ldc < std::max(1, m)) return -8;
-  if (!err) return -9;
-  return launch_syrk_tc(m, kext, PA, PB, ldp, prec, C, ldc, err, (cudaStream_t)stream);
+  if (ncols < 0 || ncols > m) return -2;
+  if (ldc < std::max(1, m)) return -9;
+  if (!err) return -10;
+  return launch_syrk_tc(m, ncols, kext, PA, PB, ldp, prec, C, ldc, err, (cudaStream_t)stream);
 }
 
 int jmg_dev_syrk_fp8(int m, int kext, const void* Q, int ldq, const signed char* e, float* C,

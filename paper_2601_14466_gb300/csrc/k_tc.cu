@@ -22,6 +22,8 @@
 // design"); the split-word tensor-core form is this library's own design.
 #include <cuda.h>
 
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace jmg {
@@ -140,36 +142,67 @@ __host__ __device__ constexpr uint32_t idesc_f16(int m, int n, int ab_fmt) {
          ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
-__global__ void __launch_bounds__(128, 1)
+// Tile b of the lower trapezoid {(ti, tj): tj <= ti < TI, tj < TJ}, enumerated
+// row by row: the first TJ rows form a triangle, every later row has TJ tiles.
+JMG_DEV void trap_index(int b, int TJ, int& ti, int& tj) {
+  const int tri = TJ * (TJ + 1) / 2;
+  if (b < tri) {
+    tri_index(b, ti, tj);
+  } else {
+    const int q = b - tri;
+    ti = TJ + q / TJ;
+    tj = q % TJ;
+  }
+}
+
+JMG_DEV void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Persistent, warp-specialised update.  192 threads:
+//   warp 0: TMA producer (one lane), warp 1: MMA issuer (one lane),
+//   warps 2-5: epilogue; warp w reads TMEM lanes 32 (w % 4) .. +31.
+// Two TMEM accumulators (2 x 128 columns): the MMAs of tile i+1 run while the
+// epilogue drains tile i.  Barriers: full/empty per smem stage, acc_full /
+// acc_empty per accumulator.
+constexpr int PSTAGES = 6;
+constexpr int PTHREADS = 192;
+constexpr int PSMEM_BYTES = PSTAGES * STAGE_BYTES + 1024 + 512;
+constexpr uint32_t PTMEM_COLS = 256;
+
+__global__ void __launch_bounds__(PTHREADS, 1)
     k_syrk_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              float* __restrict__ C, int ldc, int m, int kext, int ab_fmt, int* __restrict__ err) {
+              float* __restrict__ C, int ldc, int m, int ncols, int kext, int ab_fmt,
+              int ntiles, int TJ, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char sm_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(sm_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  uint64_t* empty = full + STAGES;
-  uint64_t* done = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + PSTAGES * STAGE_BYTES);
+  uint64_t* empty = full + PSTAGES;
+  uint64_t* acc_full = empty + PSTAGES;
+  uint64_t* acc_empty = acc_full + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   __shared__ int s_fail;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  int ti, tj;
-  tri_index(blockIdx.x, ti, tj);
   const int nk = kext / BK;
 
   if (threadIdx.x == 0) {
     s_fail = 0;
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < PSTAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 4);
+    }
     fence_mbar_init();
     prefetch_tmap(&tmA);
     prefetch_tmap(&tmB);
   }
   if (warp == 1) {
-    tmem_alloc(tmem_slot, TMEM_COLS);
+    tmem_alloc(tmem_slot, PTMEM_COLS);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -177,77 +210,115 @@ __global__ void __launch_bounds__(128, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  int issued = 0;  // producer: loads issued
-  if (warp == 0 && lane == 0) {
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1)) {
-        atomicExch(&s_fail, 1);
-        break;
+  long long issued = 0;  // producer: stage loads issued (global k-iteration count)
+  if (warp == 0) {
+    if (lane == 0) {
+      long long g = 0;
+      for (int b = blockIdx.x; b < ntiles; b += gridDim.x) {
+        int ti, tj;
+        trap_index(b, TJ, ti, tj);
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = (int)(g % PSTAGES);
+          if (g >= PSTAGES && !mbar_wait(&empty[s], (uint32_t)((g / PSTAGES) - 1) & 1)) {
+            atomicExch(&s_fail, 1);
+            break;
+          }
+          if (*(volatile int*)&s_fail) break;
+          unsigned char* sa = smem + s * STAGE_BYTES;
+          mbar_expect_tx(&full[s], STAGE_BYTES);
+          tma_load_2d(sa, &tmA, kb * BK, ti * BM, &full[s]);
+          tma_load_2d(sa + TILE_BYTES, &tmB, kb * BK, tj * BN, &full[s]);
+          ++issued;
+        }
+        if (*(volatile int*)&s_fail) break;
       }
-      if (*(volatile int*)&s_fail) break;
-      unsigned char* sa = smem + s * STAGE_BYTES;
-      unsigned char* sb = sa + TILE_BYTES;
-      mbar_expect_tx(&full[s], STAGE_BYTES);
-      tma_load_2d(sa, &tmA, kb * BK, ti * BM, &full[s]);
-      tma_load_2d(sb, &tmB, kb * BK, tj * BN, &full[s]);
-      ++issued;
     }
-  } else if (warp == 1 && lane == 0) {
-    const uint32_t idesc = idesc_f16(BM, BN, ab_fmt);
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(&full[s], (kb / STAGES) & 1)) {
-        atomicExch(&s_fail, 1);
-        break;
-      }
-      tc_fence_after();
-      const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-      const uint32_t sb = sa + TILE_BYTES;
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_f16(BM, BN, ab_fmt);
+      long long g = 0;
+      int i = 0;
+      for (int b = blockIdx.x; b < ntiles; b += gridDim.x, ++i) {
+        const int a = i & 1;
+        if (i >= 2 && !mbar_wait(&acc_empty[a], (uint32_t)((i / 2) - 1) & 1)) {
+          atomicExch(&s_fail, 1);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dacc = tmem + (uint32_t)(a * BN);
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = (int)(g % PSTAGES);
+          if (!mbar_wait(&full[s], (uint32_t)(g / PSTAGES) & 1)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+          const uint32_t sb = sa + TILE_BYTES;
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
-        // K = 16 slice: 32 bytes further along the swizzled 128-byte row
-        tc_mma_f16(tmem, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
-                   (kb > 0 || kk > 0) ? 1u : 0u);
-      }
-      tc_commit(&empty[s]);  // stage reusable once these MMAs have read it
-    }
-    tc_commit(done);  // accumulator complete (tracks every MMA issued above)
-  }
-  __syncwarp();
-
-  // ---- epilogue
-  const bool ok = mbar_wait(done, 0);
-  tc_fence_after();
-  if (!ok) atomicExch(&s_fail, 1);
-  __syncthreads();
-  const bool good = (*(volatile int*)&s_fail) == 0;
-  const int r = ti * BM + warp * 32 + lane;
-  const bool diag = (ti == tj);
-  if (good) {
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      tmem_ld_wait();
-      if (r < m) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int c = tj * BN + c0 + j;
-          if (c < m && (!diag || r >= c)) C[(size_t)c * ldc + r] -= __uint_as_float(v[j]);
+          for (int kk = 0; kk < BK / 16; ++kk)
+            tc_mma_f16(dacc, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
+                       (kb > 0 || kk > 0) ? 1u : 0u);
+          tc_commit(&empty[s]);
+        }
+        tc_commit(&acc_full[a]);
+        if (!ok) {
+          atomicExch(&s_fail, 1);
+          break;
         }
       }
     }
+  } else {
+    // epilogue warps 2..5
+    const int q = warp & 3;  // TMEM lane group of this warp
+    int i = 0;
+    for (int b = blockIdx.x; b < ntiles; b += gridDim.x, ++i) {
+      int ti, tj;
+      trap_index(b, TJ, ti, tj);
+      const int a = i & 1;
+      const bool ok = mbar_wait(&acc_full[a], (uint32_t)(i / 2) & 1);
+      tc_fence_after();
+      if (!ok || *(volatile int*)&s_fail) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
+      const int r = ti * BM + q * 32 + lane;
+      const bool diag = (ti == tj);
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN + c0), v);
+        tmem_ld_wait();
+        if (r < m) {
+          float* cp = C + r;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int c = tj * BN + c0 + j;
+            if (c < ncols && (!diag || r >= c)) cp[(size_t)c * ldc] -= __uint_as_float(v[j]);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[a]);
+    }
   }
-  // ---- teardown: on failure make sure no copy of ours is still landing
-  if (!good && warp == 0 && lane == 0) {
-    for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-      (void)mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1);
-    atomicExch(err, 1);
+  __syncwarp();
+
+  // ---- teardown
+  __syncthreads();
+  if (*(volatile int*)&s_fail) {
+    if (warp == 0 && lane == 0) {
+      // let every copy this CTA issued land before the CTA exits
+      for (long long g = (issued > PSTAGES ? issued - PSTAGES : 0); g < issued; ++g)
+        (void)mbar_wait(&full[g % PSTAGES], (uint32_t)(g / PSTAGES) & 1);
+      atomicExch(err, 1);
+    }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
+  if (warp == 1) tmem_dealloc(tmem, PTMEM_COLS);
 }
 
 }  // namespace tc
@@ -287,9 +358,10 @@ static int make_map_16(CUtensorMap* map, const void* base, int rows, int cols, i
   return r == CUDA_SUCCESS ? JMG_OK : JMG_ERR_CUDA;
 }
 
-int launch_syrk_tc(int m, int kext, const void* PA, const void* PB, int ldp, int prec, float* C,
-                   int ldc, int* err, cudaStream_t s) {
-  if (m <= 0 || kext <= 0) return JMG_OK;
+int launch_syrk_tc(int m, int ncols, int kext, const void* PA, const void* PB, int ldp, int prec,
+                   float* C, int ldc, int* err, cudaStream_t s) {
+  if (m <= 0 || ncols <= 0 || kext <= 0) return JMG_OK;
+  if (ncols > m) return JMG_ERR_UNSUPPORTED;
   if (kext % tc::BK || ldp % 64 || ldp < kext) return JMG_ERR_ALIGN;
   if ((reinterpret_cast<uintptr_t>(PA) | reinterpret_cast<uintptr_t>(PB)) & 15) return JMG_ERR_ALIGN;
   if (prec != JMG_PREC_BF16 && prec != JMG_PREC_FP16) return JMG_ERR_UNSUPPORTED;
@@ -298,15 +370,21 @@ int launch_syrk_tc(int m, int kext, const void* PA, const void* PB, int ldp, int
   CUtensorMap ma, mb;
   JMG_TRY(make_map_16(&ma, PA, m, kext, ldp, dt));
   JMG_TRY(make_map_16(&mb, PB, m, kext, ldp, dt));
-  static bool attr = false;
-  if (!attr) {
+  static int attr_dev = -1;
+  int dev = 0;
+  JMG_CUDA(cudaGetDevice(&dev));
+  static int nsm = 0;
+  if (attr_dev != dev) {
     JMG_CUDA(cudaFuncSetAttribute(tc::k_syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  tc::SMEM_BYTES));
-    attr = true;
+                                  tc::PSMEM_BYTES));
+    JMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    attr_dev = dev;
   }
-  long long tiles = tri_tiles(cdiv(m, tc::BM));
-  tc::k_syrk_tc<<<(unsigned)tiles, 128, tc::SMEM_BYTES, s>>>(ma, mb, C, ldc, m, kext,
-                                                              prec == JMG_PREC_BF16 ? 1 : 0, err);
+  const int TI = cdiv(m, tc::BM), TJ = cdiv(ncols, tc::BN);
+  const long long ntiles = (long long)TJ * (TJ + 1) / 2 + (long long)(TI - TJ) * TJ;
+  const int grid = (int)std::min<long long>(ntiles, nsm);
+  tc::k_syrk_tc<<<grid, tc::PTHREADS, tc::PSMEM_BYTES, s>>>(
+      ma, mb, C, ldc, m, ncols, kext, prec == JMG_PREC_BF16 ? 1 : 0, (int)ntiles, TJ, err);
   return launched();
 }
 

@@ -41,6 +41,21 @@ template <typename T>
 int launch_trsv_diag(int kb, int nrhs, const T* L, int lda, T* B, int ldb, int trans,
                      const int* info, cudaStream_t s);
 
+// One-launch blocked solve with the whole factor, in place on B:
+// trans == 0: L Y = B;  trans == 1: L^T X = B.  `sync` holds
+// trsv_sync_ints(n, nrhs) ints of scratch (tickets, flags, error word at the end).
+size_t trsv_sync_ints(int n, int nrhs);
+template <typename T>
+int launch_trsv_persist(int n, int nrhs, const T* L, int lda, T* B, int ldb, int trans, int* sync,
+                        const int* info, cudaStream_t s);
+// (L L^T) X = B: forward then backward with launch_trsv_persist.
+template <typename T>
+int solve_llt(int n, int nrhs, const T* L, int lda, T* B, int ldb, int* sync, const int* info,
+              cudaStream_t s) {
+  JMG_TRY(launch_trsv_persist<T>(n, nrhs, L, lda, B, ldb, 0, sync, info, s));
+  return launch_trsv_persist<T>(n, nrhs, L, lda, B, ldb, 1, sync, info, s);
+}
+
 // Blocked solves with the whole factor: L L^T X = B, in place on B.
 template <typename T>
 int blocked_potrs(int n, int nrhs, const T* L, int lda, T* B, int ldb, int nb, const int* info,
@@ -84,8 +99,10 @@ int launch_copy2d(int n, int nrhs, const double* src, int lds, double* dst, int 
 int launch_zero(double* p, size_t n, cudaStream_t s);
 
 // ---- tensor-core trailing update (k_tc.cu)
-int launch_syrk_tc(int m, int kext, const void* PA, const void* PB, int ldp, int prec, float* C,
-                   int ldc, int* err, cudaStream_t s);
+// C (m x ncols, lower trapezoid: rows >= columns) -= PA PB^T, PA/PB: m x kext
+// row-major 16-bit words; ncols <= m.
+int launch_syrk_tc(int m, int ncols, int kext, const void* PA, const void* PB, int ldp, int prec,
+                   float* C, int ldc, int* err, cudaStream_t s);
 int launch_syrk_fp8(int m, int kext, const void* Q, int ldq, const signed char* e, float* C,
                     int ldc, int* err, cudaStream_t s);
 

@@ -75,7 +75,7 @@ _SIGS = {
                       ctypes.POINTER(Stats), _P, _SZ, _P]),
     "jmg_logdet": (_I, [_I, _P, _I, _I, _P, _P]),
     "jmg_status_string": (ctypes.c_char_p, [_I]),
-    "jmg_dev_syrk_tc": (_I, [_I, _I, _P, _P, _I, _I, _P, _I, _P, _P]),
+    "jmg_dev_syrk_tc": (_I, [_I, _I, _I, _P, _P, _I, _I, _P, _I, _P, _P]),
     "jmg_dev_syrk_fp8": (_I, [_I, _I, _P, _I, _P, _P, _I, _P, _P]),
     "jmg_dev_residual_workspace": (_SZ, [_I, _I]),
     "jmg_dev_residual": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P, _SZ, _P]),
@@ -194,8 +194,9 @@ def potrs_(L: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
     _need_cuda(L, B)
     pl, lda = _colmajor(L, "L")
     pb, ldb = _colmajor(B, "B")
-    st = load().jmg_potrs(L.shape[0], B.shape[1], pl, lda, pb, ldb, JMG_F64, None, 0,
-                          _stream(L.device))
+    work = workspace(OP_POTRS, L.shape[0], B.shape[1], None, L.device)
+    st = load().jmg_potrs(L.shape[0], B.shape[1], pl, lda, pb, ldb, JMG_F64, work.data_ptr(),
+                          work.numel(), _stream(L.device))
     _chk(st, "jmg_potrs")
     return B
 
@@ -243,7 +244,7 @@ def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1
     px, ldx = _colmajor(X, "B")
     info = torch.zeros(1, dtype=torch.int32, device=A.device)
     stats = Stats()
-    if work is None and o.prec != 0:
+    if work is None:
         work = workspace(OP_POSV, n, nrhs, o, A.device)
     wp, wl = (work.data_ptr(), work.numel()) if work is not None else (None, 0)
     st = load().jmg_posv(n, nrhs, pa, lda, px, ldx, JMG_F64, info.data_ptr(), ctypes.byref(o),
@@ -302,9 +303,11 @@ def norm_inf(A: torch.Tensor) -> torch.Tensor:
     return out
 
 
-def syrk_tc_(C: torch.Tensor, PA: torch.Tensor, PB: torch.Tensor | None = None) -> torch.Tensor:
-    """C_lower -= PA PB^T on the tensor cores.  PA, PB: m x kext row-major
-    bfloat16 or float16 (kext multiple of 64); C: FP32 column-major."""
+def syrk_tc_(C: torch.Tensor, PA: torch.Tensor, PB: torch.Tensor | None = None,
+             ncols: int | None = None) -> torch.Tensor:
+    """C_lower -= PA PB^T on the tensor cores (columns < ncols, default m).
+    PA, PB: m x kext row-major bfloat16 or float16 (kext multiple of 64);
+    C: FP32 column-major."""
     _need_cuda(C, PA)
     PB = PA if PB is None else PB
     if PA.dtype not in (torch.bfloat16, torch.float16) or PB.dtype != PA.dtype:
@@ -315,8 +318,9 @@ def syrk_tc_(C: torch.Tensor, PA: torch.Tensor, PB: torch.Tensor | None = None) 
     pc, ldc = _colmajor(C, "C")
     err = torch.zeros(1, dtype=torch.int32, device=C.device)
     prec = PREC["bf16"] if PA.dtype == torch.bfloat16 else PREC["fp16"]
-    st = load().jmg_dev_syrk_tc(m, kext, PA.data_ptr(), PB.data_ptr(), kext, prec, pc, ldc,
-                                err.data_ptr(), _stream(C.device))
+    st = load().jmg_dev_syrk_tc(m, m if ncols is None else ncols, kext, PA.data_ptr(),
+                                PB.data_ptr(), kext, prec, pc, ldc, err.data_ptr(),
+                                _stream(C.device))
     _chk(st, "jmg_dev_syrk_tc")
     return err
 

@@ -67,7 +67,10 @@ def test_defaults_and_workspace():
     assert (o.nb, o.prec, o.words, o.maxit) == (128, 0, 1, 30)
     assert abs(o.tol - 1e-13) < 1e-30
     assert jmg.workspace_size(jmg.OP_POTRF, 1000, 1, o) == 0
-    assert jmg.workspace_size(jmg.OP_POSV, 1000, 4, o) == 0
+    # the plain solves only need their tickets and flags
+    assert 0 < jmg.workspace_size(jmg.OP_POSV, 1000, 4, o) <= 4096
+    assert 0 < jmg.workspace_size(jmg.OP_POTRS, 1000, 4, o) <= 4096
+    assert jmg.workspace_size(jmg.OP_POTRS, 0, 4, o) == 0
     om = jmg.default_options(prec="bf16")
     w1 = jmg.workspace_size(jmg.OP_POSV, 1000, 4, om)
     w2 = jmg.workspace_size(jmg.OP_POSV, 2000, 4, om)

@@ -77,7 +77,7 @@ def test_potrf_not_spd_info(k):
 
 
 @pytest.mark.parametrize("nrhs", [1, 3, 16, 33, 64])
-@pytest.mark.parametrize("n", [1, 100, 128, 257, 640])
+@pytest.mark.parametrize("n", [1, 100, 128, 257, 640, 2100])
 def test_potrs_matches_oracle(n, nrhs):
     A = inputs.gram_shift(n, 1.0, seed=inputs.seed_for("potrs", n))
     Lo, _ = oracle.potrf(A.numpy())
@@ -161,10 +161,12 @@ def test_norm_inf_matches_oracle(n):
     assert abs(g - o) <= 4 * n * U64 * o
 
 
-@pytest.mark.parametrize("m", [1, 100, 128, 129, 300, 511])
+@pytest.mark.parametrize("m,ncols", [(1, 1), (100, 100), (128, 128), (129, 129), (300, 300),
+                                     (511, 511), (2600, 2600), (4000, 4000), (2600, 700),
+                                     (1000, 128)])
 @pytest.mark.parametrize("kext", [64, 192])
 @pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
-def test_syrk_tc_exact_integers(m, kext, dtype):
+def test_syrk_tc_exact_integers(m, ncols, kext, dtype):
     # small integers: products and FP32 sums are exact, so the tensor-core
     # update must equal the integer result bit for bit
     g = torch.Generator().manual_seed(m * 1000 + kext)
@@ -175,12 +177,13 @@ def test_syrk_tc_exact_integers(m, kext, dtype):
     Cd, _ = to_dev_colmajor(C0.to(torch.float32).to(torch.float64))
     Cf = Cd.to(torch.float32)
     Cf = Cf.t().contiguous().t()
-    err = jmg.syrk_tc_(Cf, PA.to(DEV).to(dtype).contiguous(), PB.to(DEV).to(dtype).contiguous())
+    err = jmg.syrk_tc_(Cf, PA.to(DEV).to(dtype).contiguous(), PB.to(DEV).to(dtype).contiguous(),
+                       ncols=ncols)
     torch.cuda.synchronize()
     assert int(err.item()) == 0
     got = Cf.double().cpu().numpy()
     w = want.numpy()
-    lo = np.tril_indices(m)
-    assert np.array_equal(got[lo], w[lo])
-    up = np.triu_indices(m, 1)
-    assert np.array_equal(got[up], C0.numpy()[up]), "upper triangle was written"
+    touched = np.tril(np.ones((m, m), dtype=bool))
+    touched[:, ncols:] = False
+    assert np.array_equal(got[touched], w[touched])
+    assert np.array_equal(got[~touched], C0.numpy()[~touched]), "outside the trapezoid was written"
