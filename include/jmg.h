@@ -22,7 +22,9 @@
  *  - `info` words are device pointers written asynchronously: 0, or k > 0 when
  *    the leading minor of order k is not positive definite (its pivot is
  *    <= 0 or NaN).  After a failure the factor is left partly computed, as in
- *    LAPACK, and later kernels of the same call do nothing.
+ *    LAPACK, and later kernels of the same call do nothing.  info = -1 reports
+ *    an internal error: a device-side wait of the solve ran out (the kernels
+ *    never spin without a time limit), and B is then not a solution.
  */
 #ifndef JMG_H
 #define JMG_H

@@ -156,11 +156,12 @@ static int sync_read(void* host, const void* dev, size_t bytes, cudaStream_t s) 
 }
 
 // M^{-1} R in FP32 with per-column scaling, added to X (FP64): X += s * (L L^T)^{-1} (R / s)
+// `status` is a device int set to -1 if a device-side wait of the solve ran out.
 static int precond_update(int n, int nrhs, const float* W, int ldw, const double* R,
-                          const double* colmax_r, float* D, double* X, int* sync,
+                          const double* colmax_r, float* D, double* X, int* sync, int* status,
                           cudaStream_t s) {
   JMG_TRY(launch_scale_to_f32(n, nrhs, R, n, colmax_r, D, n, s));
-  JMG_TRY(solve_llt<float>(n, nrhs, W, ldw, D, n, sync, nullptr, s));
+  JMG_TRY(solve_llt<float>(n, nrhs, W, ldw, D, n, sync, status, s));
   JMG_TRY(launch_axpy_f32(n, nrhs, D, n, colmax_r, X, n, s));
   return JMG_OK;
 }
@@ -177,7 +178,7 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
   double* eta = at<double>(work, p.off_eta);
   double* anorm = at<double>(work, p.off_anorm);
   double* rowsum = at<double>(work, p.off_rowsum);
-  int* ints = at<int>(work, p.off_ints);  // [0] info_f, [1] err
+  int* ints = at<int>(work, p.off_ints);  // [0] info_f, [1] factor err, [2] solve status
   jmg_stats local{};
   jmg_stats& S = st ? *st : local;
   S = jmg_stats{};
@@ -223,7 +224,8 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
     k_copy_colmax<<<grid, 256, 0, s>>>(n, B, ldb, R, colmax);
     JMG_TRY(launched());
   }
-  JMG_TRY(precond_update(n, nrhs, W, p.ldw, R, colmax, D, X, at<int>(work, p.off_sync), s));
+  JMG_TRY(precond_update(n, nrhs, W, p.ldw, R, colmax, D, X, at<int>(work, p.off_sync), &ints[2],
+                           s));
   double t2 = now_ms();
 
   // FP64 iterative refinement
@@ -259,9 +261,15 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
       break;
     }
     prev = eh[0];
-    JMG_TRY(precond_update(n, nrhs, W, p.ldw, R, colmax, D, X, at<int>(work, p.off_sync), s));
+    JMG_TRY(precond_update(n, nrhs, W, p.ldw, R, colmax, D, X, at<int>(work, p.off_sync), &ints[2],
+                           s));
   }
   S.iters = it;
+  {
+    int hs3[3] = {0, 0, 0};
+    JMG_TRY(sync_read(hs3, ints, sizeof(int) * 3, s));
+    if (hs3[2] != 0) S.status = JMG_ERR_TIMEOUT;
+  }
   if (o.timing) {
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);

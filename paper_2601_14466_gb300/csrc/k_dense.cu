@@ -13,69 +13,90 @@ namespace jmg {
 long long g_launches = 0;
 
 // ============================================================================
-// potf2: Cholesky of one diagonal block (kb <= NBMAX) in shared memory, FP64.
-// Storage type T (double: plain path; float: the FP32 working matrix of the
-// mixed path).  Right-looking within the block with ONE barrier per column:
-//   - column j's pivot l_jj = sqrt(d_j) and 1/l_jj were computed before the
-//     barrier by the thread that applied the last update to d_j;
-//   - every thread (row r, column group g) writes l_rj = a_rj / l_jj straight
-//     to global memory and applies a_rc -= (a_rj / d_j) * a_cj, which equals
-//     l_rj * l_cj, for its columns c in (j, r] -- column j itself is only read;
-//   - the thread owning row j+1 then finishes d_{j+1} and its pivot.
-// A pivot that is not > 0 (or NaN) records info = koff + j + 1 and stops;
-// the columns before it are final, the rest keep their input values.
+// Diagonal-block factorisation L_kk L_kk^T = A_kk (kb <= 128), in place, all
+// arithmetic in FP64 (the block is held as FP64 in shared memory whatever the
+// storage type T: double for the plain path, float for the FP32 working matrix
+// of the mixed path).
+//
+// Right-looking with one barrier per column.  At column j every warp owns a
+// set of columns c > j (round robin) with lane = row; it forms
+// w_c = a_cj / d_j once and applies a_rc -= a_rj * w_c, which equals
+// l_rj * l_cj, to its rows r >= c.  Column j itself is only read during the
+// step, so no second barrier is needed; l_rj = a_rj / l_jj goes straight to
+// global memory.  Warp 0 updates column j+1 first and lane 0 starts the next
+// pivot (sqrt and reciprocal: exact for the plain path; FP32 seed plus one
+// Newton step of Newton's method for x^{-1/2} in the mixed path, whose output
+// is rounded to FP32 anyway) before its remaining columns, so the pivot
+// latency overlaps the update.  A pivot that is not > 0 (or NaN) records
+// info = koff + j + 1; columns before it are final, the rest keep their input.
 // ============================================================================
-template <typename T, int NBMAX>
-__global__ void __launch_bounds__(256) k_potf2(T* __restrict__ A, int lda, int kb, int koff,
-                                               int* __restrict__ info) {
-  extern __shared__ double sm_potf2[];
-  __shared__ double s_ljj[NBMAX], s_inv[NBMAX];
+template <typename T>
+__global__ void __launch_bounds__(256) k_potrf_diag(T* __restrict__ A, int lda, int kb, int koff,
+                                                    int* __restrict__ info) {
+  extern __shared__ __align__(16) unsigned char sm_diag[];
+  double* sa = reinterpret_cast<double*>(sm_diag);  // kb x (kb+1), column-major
+  __shared__ double s_ljj[128], s_inv[128];
   __shared__ int fail;
   if (*(volatile int*)info != 0) return;  // an earlier block already failed
   const int ld = kb + 1;
-  double* s = sm_potf2;
-  const int t = threadIdx.x;
-  for (int idx = t; idx < kb * kb; idx += blockDim.x) {
-    int i = idx % kb, j = idx / kb;
-    if (i >= j) s[j * ld + i] = (double)A[(size_t)j * lda + i];
-  }
-  __syncthreads();
-  if (t == 0) {
-    fail = 0;
-    const double d = s[0];
-    if (!(d > 0.0)) {
-      fail = 1;
-    } else {
-      const double l = sqrt(d);
-      s_ljj[0] = l;
-      s_inv[0] = 1.0 / l;
+  const int t = threadIdx.x, warp = t / 32, lane = t % 32;
+  constexpr bool kExact = sizeof(T) == 8;
+  for (int base = 0; base < kb * kb; base += 256 * 16) {  // 16 independent loads per thread
+    T v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int idx = base + t + 256 * q;
+      const int i = idx % kb, j = idx / kb;
+      v[q] = (idx < kb * kb && i >= j) ? A[(size_t)j * lda + i] : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int idx = base + t + 256 * q;
+      if (idx < kb * kb) sa[(idx / kb) * ld + idx % kb] = (double)v[q];
     }
   }
   __syncthreads();
-  constexpr int G = 256 / NBMAX;  // column groups
-  const int r = t % NBMAX, g = t / NBMAX;
+  auto pivot = [&](int j) {  // called by one thread once a_jj is final
+    const double d = sa[j * ld + j];
+    if (!(d > 0.0)) {
+      fail = j + 1;
+      return;
+    }
+    double l, inv;
+    if (kExact) {
+      l = sqrt(d);
+      inv = 1.0 / l;
+    } else {
+      const double y0 = (double)rsqrtf((float)d);
+      inv = y0 * fma(-0.5 * d, y0 * y0, 1.5);  // one Newton step for d^{-1/2}
+      l = d * inv;
+    }
+    s_ljj[j] = l;
+    s_inv[j] = inv;
+  };
+  if (t == 0) {
+    fail = 0;
+    pivot(0);
+  }
+  __syncthreads();
   for (int j = 0; j < kb; ++j) {
     if (fail) break;
-    if (r >= j && r < kb) {
-      const double inv = s_inv[j];
-      const double arj = s[j * ld + r];
-      const double lrj = (r == j) ? s_ljj[j] : arj * inv;
-      if (g == 0) A[(size_t)j * lda + r] = (T)lrj;
-      if (r > j) {
-        const double q = lrj * inv;  // a_rj / d_j
-#pragma unroll 4
-        for (int c = j + 1 + g; c <= r; c += G) s[c * ld + r] -= q * s[j * ld + c];
-        if (g == 0 && r == j + 1) {  // this thread applied the last update to d_{j+1}
-          const double d = s[r * ld + r];
-          if (!(d > 0.0)) {
-            fail = r + 1;
-          } else {
-            const double l = sqrt(d);
-            s_ljj[r] = l;
-            s_inv[r] = 1.0 / l;
-          }
-        }
+    const double inv = s_inv[j];
+    const double inv2 = inv * inv;
+    // column j of L: l_rj = a_rj / l_jj (rows j..kb-1), straight to global
+    for (int r = j + t; r < kb; r += 256) {
+      const double lrj = (r == j) ? s_ljj[j] : sa[j * ld + r] * inv;
+      A[(size_t)j * lda + r] = (T)lrj;
+    }
+    // trailing update, warp w owns columns c = j+1+w, j+1+w+8, ...
+    for (int c = j + 1 + warp; c < kb; c += 8) {
+      const double wc = sa[j * ld + c] * inv2;  // a_cj / d_j
+      int r = c + lane;
+      if (r < kb) {
+        sa[c * ld + r] -= sa[j * ld + r] * wc;
+        if (c == j + 1 && lane == 0) pivot(j + 1);  // a_{j+1,j+1} is final now
       }
+      for (r += 32; r < kb; r += 32) sa[c * ld + r] -= sa[j * ld + r] * wc;
     }
     __syncthreads();
   }
@@ -85,15 +106,14 @@ __global__ void __launch_bounds__(256) k_potf2(T* __restrict__ A, int lda, int k
 template <typename T>
 static int potf2_impl(T* A, int lda, int kb, int koff, int* info, cudaStream_t s) {
   size_t smem = (size_t)kb * (kb + 1) * sizeof(double);
-  if (kb <= 64) {
-    auto k = k_potf2<T, 64>;
-    JMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k<<<1, 256, smem, s>>>(A, lda, kb, koff, info);
-  } else {
-    auto k = k_potf2<T, 128>;
-    JMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k<<<1, 256, smem, s>>>(A, lda, kb, koff, info);
+  auto k = k_potrf_diag<T>;
+  static int attr[2] = {0, 0};
+  if (!attr[sizeof(T) == 8]) {
+    JMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(128 * 129 * sizeof(double))));
+    attr[sizeof(T) == 8] = 1;
   }
+  k<<<1, 256, smem, s>>>(A, lda, kb, koff, info);
   return launched();
 }
 int launch_potf2(double* A, int lda, int kb, int koff, int* info, cudaStream_t s) {
@@ -121,13 +141,33 @@ __global__ void __launch_bounds__(256) k_trsm(T* __restrict__ A21, int lda, int 
   const int ldx = BR + 1;
   const int t = threadIdx.x;
   const int r0 = blockIdx.x * BR;
-  for (int idx = t; idx < kb * kb; idx += blockDim.x) {
-    int i = idx % kb, j = idx / kb;
-    Ls[j * ldl + i] = (i >= j) ? Lkk[(size_t)j * lda + i] : T(0);
+  for (int base = 0; base < kb * kb; base += 256 * 16) {  // 16 independent loads per thread
+    T v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int idx = base + t + 256 * q;
+      const int i = idx % kb, j = idx / kb;
+      v[q] = (idx < kb * kb && i >= j) ? Lkk[(size_t)j * lda + i] : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int idx = base + t + 256 * q;
+      if (idx < kb * kb) Ls[(idx / kb) * ldl + idx % kb] = v[q];
+    }
   }
-  for (int idx = t; idx < BR * kb; idx += blockDim.x) {
-    int i = idx % BR, j = idx / BR;
-    Xs[j * ldx + i] = (r0 + i < m) ? A21[(size_t)j * lda + r0 + i] : T(0);
+  for (int base = 0; base < BR * kb; base += 256 * 16) {
+    T v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int idx = base + t + 256 * q;
+      const int i = idx % BR, j = idx / BR;
+      v[q] = (idx < BR * kb && r0 + i < m) ? A21[(size_t)j * lda + r0 + i] : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int idx = base + t + 256 * q;
+      if (idx < BR * kb) Xs[(idx / BR) * ldx + idx % BR] = v[q];
+    }
   }
   __syncthreads();
   constexpr int G = 256 / BR;
@@ -159,8 +199,84 @@ int launch_trsm(double* A21, int lda, int m, int kb, const double* Lkk, const in
                 cudaStream_t s) {
   return trsm_impl<double, 32>(A21, lda, m, kb, Lkk, info, s);
 }
+// FP32 panel TRSM of the mixed path (kb == KB): one thread per row solves
+// x Lkk^T = a in 32-column chunks.  Chunk J starts from a_J, subtracts the
+// finished chunks K < J (x_K L_JK^T, read back from shared memory where this
+// thread parked them) and then solves with the diagonal 32 x 32 block
+// right-looking (x_k = a_k / L_kk, a_c -= x_k L_ck).  Lkk sits in shared memory
+// transposed (Lt[k][c] = L[c][k]) so every warp reads it as broadcasts; only
+// the 32 values of the current chunk live in registers.
+template <int KB>
+__global__ void __launch_bounds__(128) k_trsm_rows(float* __restrict__ A21, int lda, int m,
+                                                   const float* __restrict__ Lkk,
+                                                   const int* __restrict__ info) {
+  if (*(volatile const int*)info != 0) return;
+  extern __shared__ __align__(16) float sm_trows[];
+  float(*Lt)[KB] = reinterpret_cast<float(*)[KB]>(sm_trows);       // KB x KB
+  float(*Xs)[128] = reinterpret_cast<float(*)[128]>(sm_trows + KB * KB);  // (KB-32) x 128
+  float* rinv = sm_trows + KB * KB + (KB - 32) * 128;
+  const int t = threadIdx.x;
+  for (int base = 0; base < KB * KB; base += 128 * 16) {
+    float v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int idx = base + t + 128 * q;
+      const int c = idx % KB, k = idx / KB;  // column k of L, row c
+      v[q] = (c >= k) ? Lkk[(size_t)k * lda + c] : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int idx = base + t + 128 * q;
+      Lt[idx / KB][idx % KB] = v[q];
+    }
+  }
+  __syncthreads();
+  if (t < KB) rinv[t] = 1.0f / Lt[t][t];
+  __syncthreads();
+  const int r = blockIdx.x * 128 + t;
+  if (r >= m) return;
+  for (int J = 0; J < KB / 32; ++J) {
+    const int j0 = J * 32;
+    float x[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) x[c] = A21[(size_t)(j0 + c) * lda + r];
+    for (int k = 0; k < j0; ++k) {
+      const float xk = Xs[k][t];
+      const float4* lrow = reinterpret_cast<const float4*>(&Lt[k][j0]);
+#pragma unroll
+      for (int c4 = 0; c4 < 8; ++c4) {
+        const float4 l = lrow[c4];
+        x[4 * c4 + 0] -= xk * l.x;
+        x[4 * c4 + 1] -= xk * l.y;
+        x[4 * c4 + 2] -= xk * l.z;
+        x[4 * c4 + 3] -= xk * l.w;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      x[k] *= rinv[j0 + k];
+#pragma unroll
+      for (int c = k + 1; c < 32; ++c) x[c] -= x[k] * Lt[j0 + k][j0 + c];
+    }
+    if (J < KB / 32 - 1) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) Xs[j0 + c][t] = x[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 32; ++c) A21[(size_t)(j0 + c) * lda + r] = x[c];
+  }
+}
+
 int launch_trsm(float* A21, int lda, int m, int kb, const float* Lkk, const int* info,
                 cudaStream_t s) {
+  if (m <= 0) return JMG_OK;
+  if (kb == 128 || kb == 64) {
+    auto k = (kb == 128) ? k_trsm_rows<128> : k_trsm_rows<64>;
+    const size_t smem = sizeof(float) * ((size_t)kb * kb + (size_t)(kb - 32) * 128 + kb);
+    JMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k<<<cdiv(m, 128), 128, smem, s>>>(A21, lda, m, Lkk, info);
+    return launched();
+  }
   return trsm_impl<float, 64>(A21, lda, m, kb, Lkk, info, s);
 }
 

@@ -291,11 +291,19 @@ __global__ void __launch_bounds__(PTHREADS, 1)
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN + c0), v);
         tmem_ld_wait();
         if (r < m) {
+          // all 32 loads first (independent, coalesced across the warp), then the stores
           float* cp = C + r;
+          const int cb = tj * BN + c0;
+          float old[32];
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            const int c = tj * BN + c0 + j;
-            if (c < ncols && (!diag || r >= c)) cp[(size_t)c * ldc] -= __uint_as_float(v[j]);
+            const int c = cb + j;
+            old[j] = (c < ncols && (!diag || r >= c)) ? cp[(size_t)c * ldc] : 0.0f;
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int c = cb + j;
+            if (c < ncols && (!diag || r >= c)) cp[(size_t)c * ldc] = old[j] - __uint_as_float(v[j]);
           }
         }
       }

@@ -55,9 +55,9 @@ __global__ void __launch_bounds__(256) k_trsv_persist(int n, int nrhs, const T* 
                                                       int trans, int* __restrict__ tickets,
                                                       int* __restrict__ flags,
                                                       int* __restrict__ err,
-                                                      const int* __restrict__ info) {
+                                                      int* __restrict__ info) {
   using namespace trsv;
-  if (info && *(volatile const int*)info != 0) return;  // no factor: leave B alone
+  if (info && *(volatile int*)info != 0) return;  // no factor: leave B alone
   extern __shared__ __align__(16) unsigned char sm_raw_trsv[];
   Smem<T>& S = *reinterpret_cast<Smem<T>*>(sm_raw_trsv);
   const int nblk = cdiv_dev(n, NBK);
@@ -87,63 +87,92 @@ __global__ void __launch_bounds__(256) k_trsv_persist(int n, int nrhs, const T* 
         acc[q][p] = (i < rows && c < ncol) ? B[(size_t)(c0 + c) * ldb + r0 + i] : T(0);
       }
 
+    // ---- off-diagonal products as a stream of 32-column chunks; the next
+    // chunk of L (final, no flag needed) is prefetched into registers while
+    // the current one is multiplied.  Y chunks are read after the flag of
+    // their block was acquired.
+    constexpr int LQ = KC * NBK / 256, YQ = KC * NR / 256;
     const int ndep = trans ? (nblk - 1 - b) : b;
-    for (int d = 0; d < ndep; ++d) {
+    T lv[LQ];
+    auto load_L = [&](int dd, int kk0) {
+      const int j = trans ? (nblk - 1 - dd) : dd;
+      const int j0 = j * NBK, jrows = min(NBK, n - j0);
+#pragma unroll
+      for (int q = 0; q < LQ; ++q) {
+        const int idx = t + 256 * q;
+        const int i = trans ? idx / KC : idx % NBK;
+        const int kk = trans ? idx % KC : idx / NBK;
+        const int gk = kk0 + kk;
+        T v = T(0);
+        if (i < rows && gk < jrows)
+          v = trans ? L[(size_t)(r0 + i) * lda + j0 + gk] : L[(size_t)(j0 + gk) * lda + r0 + i];
+        lv[q] = v;
+      }
+    };
+    int d = 0, k0 = 0;
+    if (ndep > 0) load_L(0, 0);
+    while (d < ndep) {
       const int j = trans ? (nblk - 1 - d) : d;
-      if (t == 0) {
-        if (!ld_acquire(&flag[j])) {
-          const uint64_t t0 = globaltimer_ns();
-          while (!ld_acquire(&flag[j])) {
-            if (globaltimer_ns() - t0 > WAIT_NS || *(volatile int*)err) {
-              S.abort = 1;
-              atomicExch(err, 1);
-              break;
+      const int j0 = j * NBK, jrows = min(NBK, n - j0);
+      if (k0 == 0) {
+        if (t == 0) {
+          if (!ld_acquire(&flag[j])) {
+            const uint64_t t0 = globaltimer_ns();
+            while (!ld_acquire(&flag[j])) {
+              if (globaltimer_ns() - t0 > WAIT_NS || *(volatile int*)err) {
+                S.abort = 1;
+                atomicExch(err, 1);
+                if (info) atomicCAS(info, 0, -1);  // the solve is incomplete
+                break;
+              }
+              __nanosleep(64);
             }
-            __nanosleep(64);
           }
         }
+        __syncthreads();
+        if (S.abort) break;
+      }
+      T yv[YQ];
+#pragma unroll
+      for (int q = 0; q < YQ; ++q) {
+        const int idx = t + 256 * q;
+        const int kk = idx % KC, c = idx / KC, gk = k0 + kk;
+        yv[q] = (gk < jrows && c < ncol) ? ldcg(&B[(size_t)(c0 + c) * ldb + j0 + gk]) : T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < LQ; ++q) {
+        const int idx = t + 256 * q;
+        const int i = trans ? idx / KC : idx % NBK;
+        const int kk = trans ? idx % KC : idx / NBK;
+        S.Ls[kk][i] = lv[q];
+      }
+#pragma unroll
+      for (int q = 0; q < YQ; ++q) {
+        const int idx = t + 256 * q;
+        S.Ys[idx % KC][idx / KC] = yv[q];
       }
       __syncthreads();
-      if (S.abort) break;
-      const int j0 = j * NBK, jrows = min(NBK, n - j0);
-      for (int k0 = 0; k0 < jrows; k0 += KC) {
-        // off-diagonal chunk: forward L[r0+i, j0+k0+kk]; backward L[j0+k0+kk, r0+i]
-        for (int idx = t; idx < KC * NBK; idx += 256) {
-          int i, kk;
-          if (!trans) {
-            i = idx % NBK;
-            kk = idx / NBK;
-          } else {
-            kk = idx % KC;
-            i = idx / KC;
-          }
-          const int gk = k0 + kk;
-          T v = T(0);
-          if (i < rows && gk < jrows)
-            v = trans ? L[(size_t)(r0 + i) * lda + j0 + gk] : L[(size_t)(j0 + gk) * lda + r0 + i];
-          S.Ls[kk][i] = v;
-        }
-        for (int idx = t; idx < KC * NR; idx += 256) {
-          const int kk = idx % KC, c = idx / KC;
-          const int gk = k0 + kk;
-          S.Ys[kk][c] =
-              (gk < jrows && c < ncol) ? ldcg(&B[(size_t)(c0 + c) * ldb + j0 + gk]) : T(0);
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int kk = 0; kk < KC; ++kk) {
-          T a[4], y[2];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) a[q] = S.Ls[kk][tx + 32 * q];
-#pragma unroll
-          for (int p = 0; p < 2; ++p) y[p] = S.Ys[kk][ty + 8 * p];
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int p = 0; p < 2; ++p) acc[q][p] -= a[q] * y[p];
-        }
-        __syncthreads();
+      int nd = d, nk0 = k0 + KC;
+      if (nk0 >= jrows) {
+        nd = d + 1;
+        nk0 = 0;
       }
+      if (nd < ndep) load_L(nd, nk0);
+#pragma unroll 8
+      for (int kk = 0; kk < KC; ++kk) {
+        T a[4], y[2];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[q] = S.Ls[kk][tx + 32 * q];
+#pragma unroll
+        for (int p = 0; p < 2; ++p) y[p] = S.Ys[kk][ty + 8 * p];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int p = 0; p < 2; ++p) acc[q][p] -= a[q] * y[p];
+      }
+      __syncthreads();
+      d = nd;
+      k0 = nk0;
     }
     if (S.abort) break;
 
@@ -152,11 +181,19 @@ __global__ void __launch_bounds__(256) k_trsv_persist(int n, int nrhs, const T* 
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int p = 0; p < 2; ++p) S.Ss[tx + 32 * q][ty + 8 * p] = acc[q][p];
-    for (int idx = t; idx < NBK * NBK; idx += 256) {
-      const int i = idx % NBK, k = idx / NBK;  // column k, row i: coalesced down a column
-      T v = T(0);
-      if (i < rows && k < rows && i >= k) v = L[(size_t)(r0 + k) * lda + r0 + i];
-      S.Ld[i][k] = v;
+    for (int base = 0; base < NBK * NBK; base += 256 * 16) {  // 16 loads in flight
+      T v[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int idx = base + t + 256 * q;
+        const int i = idx % NBK, k = idx / NBK;  // column k, row i: coalesced down a column
+        v[q] = (i < rows && k < rows && i >= k) ? L[(size_t)(r0 + k) * lda + r0 + i] : T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int idx = base + t + 256 * q;
+        S.Ld[idx % NBK][idx / NBK] = v[q];
+      }
     }
     __syncthreads();
     if (t < NBK) S.rinv[t] = (t < rows) ? T(1) / S.Ld[t][t] : T(0);
@@ -231,13 +268,13 @@ size_t trsv_sync_ints(int n, int nrhs) {
 
 template <typename T>
 int launch_trsv_persist(int n, int nrhs, const T* L, int lda, T* B, int ldb, int trans,
-                        int* sync, const int* info, cudaStream_t s) {
+                        int* sync, int* info, cudaStream_t s) {
   if (n <= 0 || nrhs <= 0) return JMG_OK;
   const int groups = cdiv(nrhs, trsv::NR), nblk = cdiv(n, trsv::NBK);
   int* tickets = sync;
   int* flags = sync + groups;
   int* err = flags + (size_t)groups * nblk;
-  JMG_CUDA(cudaMemsetAsync(sync, 0, sizeof(int) * (groups * (size_t)(1 + nblk)), s));
+  JMG_CUDA(cudaMemsetAsync(sync, 0, sizeof(int) * trsv_sync_ints(n, nrhs), s));
   const size_t smem = sizeof(trsv::Smem<T>);
   static int done_attr[2] = {0, 0};
   auto k = k_trsv_persist<T>;
@@ -258,8 +295,8 @@ int launch_trsv_persist(int n, int nrhs, const T* L, int lda, T* B, int ldb, int
   return launched();
 }
 template int launch_trsv_persist<float>(int, int, const float*, int, float*, int, int, int*,
-                                        const int*, cudaStream_t);
+                                        int*, cudaStream_t);
 template int launch_trsv_persist<double>(int, int, const double*, int, double*, int, int, int*,
-                                         const int*, cudaStream_t);
+                                         int*, cudaStream_t);
 
 }  // namespace jmg

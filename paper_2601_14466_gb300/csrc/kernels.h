@@ -47,10 +47,10 @@ int launch_trsv_diag(int kb, int nrhs, const T* L, int lda, T* B, int ldb, int t
 size_t trsv_sync_ints(int n, int nrhs);
 template <typename T>
 int launch_trsv_persist(int n, int nrhs, const T* L, int lda, T* B, int ldb, int trans, int* sync,
-                        const int* info, cudaStream_t s);
+                        int* info, cudaStream_t s);
 // (L L^T) X = B: forward then backward with launch_trsv_persist.
 template <typename T>
-int solve_llt(int n, int nrhs, const T* L, int lda, T* B, int ldb, int* sync, const int* info,
+int solve_llt(int n, int nrhs, const T* L, int lda, T* B, int ldb, int* sync, int* info,
               cudaStream_t s) {
   JMG_TRY(launch_trsv_persist<T>(n, nrhs, L, lda, B, ldb, 0, sync, info, s));
   return launch_trsv_persist<T>(n, nrhs, L, lda, B, ldb, 1, sync, info, s);
