@@ -68,10 +68,13 @@ typedef struct {
   int prec;         /* jmg_prec                                                     */
   int words;        /* split words per tensor-core operand, 1..3 (BF16 / FP16)      */
   double tol;       /* target normwise backward error of posv (mixed modes)         */
-  int maxit;        /* maximum refinement iterations                                */
+  int maxit;        /* maximum refinement iterations (IR steps + PCG steps)         */
   int refine;       /* jmg_refine                                                   */
   int shift_retry;  /* low-precision breakdown: retry with a diagonal shift (0/1)   */
   int timing;       /* 1: time the FP64 residual kernel with CUDA events (stats)    */
+  int reuse_factor; /* mixed posv only: 1 = skip the factorisation and refine with  */
+                    /* the factor that an earlier jmg_posv call with the same A, n  */
+                    /* and options left in `work` (the adjoint solve of autograd)   */
 } jmg_options;
 
 /* Host-side report of one posv call (filled when the call returns). */
@@ -86,12 +89,14 @@ typedef struct {
   double shift;     /* diagonal shift of the factor (0 if none)                     */
   double anorm;     /* ||A||_inf                                                     */
   double t_factor_ms, t_solve_ms, t_refine_ms; /* host-timed phases (0 if not synced) */
-  double t_resid_gpu_ms; /* with opt->timing: summed CUDA-event time of the residual GEMM */
-  int n_resid;           /* number of residual evaluations                            */
+  double t_resid_gpu_ms; /* with opt->timing: summed CUDA-event time of the FP64 A*X GEMM  */
+  int n_resid;           /* number of FP64 A*X evaluations (residuals and PCG products)  */
+  int n_hist;            /* entries of eta_hist written (may exceed 32: first 32 kept)   */
+  double eta_hist[32];   /* max_j backward error after each residual / PCG step          */
 } jmg_stats;
 
 /* Fill *opt with the defaults: nb 128, NB 128, prec NATIVE, words 1, tol 1e-13,
- * maxit 30, refine AUTO, shift_retry 1, timing 0. */
+ * maxit 50, refine AUTO, shift_retry 1, timing 0, reuse_factor 0. */
 void jmg_default_options(jmg_options* opt);
 
 /* Bytes of `work` that the call (op, n, nrhs, dtype, opt) needs; 0 is valid. */
@@ -144,6 +149,18 @@ int jmg_posv(int n, int nrhs, void* A, int lda, void* B, int ldb, int dtype, int
  *   out     device double, written asynchronously
  */
 int jmg_logdet(int n, const void* L, int lda, int dtype, double* out, void* stream);
+
+/*
+ * sym_grad -- adjoint of X = A^{-1} B with respect to the symmetric A:
+ *     Abar = -(Bbar X^T + X Bbar^T) / 2         (n x n, full symmetric, FP64)
+ * where Bbar = A^{-1} Xbar is the adjoint solve.  The paper exposes potrs as a
+ * primitive that composes with the framework's transformations ("Summary");
+ * this is reverse-mode differentiation of it.  Bbar, X: n x nrhs column-major
+ * (ldb, ldx >= n); Abar: ldab >= n, every element of the n x n block written.
+ * Asynchronous.
+ */
+int jmg_sym_grad(int n, int nrhs, const double* Bbar, int ldb, const double* X, int ldx,
+                 double* Abar, int ldab, void* stream);
 
 /* Human-readable name of a status code. */
 const char* jmg_status_string(int status);

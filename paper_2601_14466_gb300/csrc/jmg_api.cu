@@ -55,7 +55,11 @@ static Plan plan_posv_mixed(int n, int nrhs, const jmg_options& o) {
   p.kext = o.nb * split_pairs(o.words);
   p.ldp = (int)round_up((size_t)p.kext, 64);
   p.splits = residual_splits(n, nrhs > 0 ? nrhs : 1);
+  // the factor and what a refine-only call (reuse_factor) needs come first, at
+  // offsets that do not depend on nrhs
   p.off_W = take(sizeof(float) * (size_t)p.ldw * N);
+  p.off_anorm = take(sizeof(double) * 2);  // [0] ||A||_inf, [1] shift of the factor
+  p.off_ints = take(sizeof(int) * 8);
   p.off_PA = take(2 * N * p.ldp);
   p.off_PB = take(2 * N * p.ldp);
   p.off_X = take(sizeof(double) * N * R);
@@ -64,9 +68,7 @@ static Plan plan_posv_mixed(int n, int nrhs, const jmg_options& o) {
   p.off_part = take(sizeof(double) * N * R * p.splits);
   p.off_colmax = take(sizeof(double) * 3 * R);
   p.off_eta = take(sizeof(double) * (1 + R));
-  p.off_anorm = take(sizeof(double) * 2);
   p.off_rowsum = take(sizeof(double) * (N > 0 ? N : 1));
-  p.off_ints = take(sizeof(int) * 8);
   p.off_Z = take(sizeof(double) * N * R);
   p.off_P = take(sizeof(double) * N * R);
   p.off_Q = take(sizeof(double) * N * R);
@@ -166,119 +168,244 @@ static int precond_update(int n, int nrhs, const float* W, int ldw, const double
   return JMG_OK;
 }
 
+// Refinement state of one mixed solve (device buffers carved from `work`).
+struct MixedCtx {
+  int n, nrhs, lda, ldb;
+  const double* A;
+  double* B;
+  const Plan* p;
+  const jmg_options* o;
+  void* work;
+  cudaStream_t s;
+  float* W;
+  double *X, *R, *Z, *P, *Q, *part, *colmax, *eta, *dsc, *rowsum, *rz, *rz_new, *pq;
+  float* D;
+  int* ints;  // [0] factor info, [1] factor err, [2] solve status, [3] PCG breakdown
+  int* sync;
+  cudaEvent_t ev[2];
+  jmg_stats* S;
+  std::vector<double> eh;
+};
+
+static void hist(MixedCtx& c, double e) {
+  if (c.S->n_hist < 32) c.S->eta_hist[c.S->n_hist] = e;
+  c.S->n_hist++;
+}
+
+// R = B - A X (true residual), eta -> host; returns max eta in c.eh[0]
+static int true_residual(MixedCtx& c) {
+  JMG_TRY(launch_residual(c.n, c.nrhs, c.A, c.lda, c.X, c.n, c.B, c.ldb, c.R, c.n, c.colmax,
+                          c.part, c.p->splits, c.s, c.ev[0], c.ev[1]));
+  JMG_TRY(launch_eta(c.nrhs, c.colmax, c.dsc, c.eta, c.s));
+  JMG_TRY(sync_read(c.eh.data(), c.eta, sizeof(double) * (1 + c.nrhs), c.s));
+  c.S->n_resid++;
+  if (c.o->timing) {
+    float ms = 0.f;
+    JMG_CUDA(cudaEventElapsedTime(&ms, c.ev[0], c.ev[1]));
+    c.S->t_resid_gpu_ms += ms;
+  }
+  return JMG_OK;
+}
+
+// Z = M^{-1} R with the FP32 factor (per-column scaling by ||r_c||)
+static int precond_to(MixedCtx& c, double* Zout) {
+  JMG_TRY(launch_scale_to_f32(c.n, c.nrhs, c.R, c.n, c.colmax, c.D, c.n, c.s));
+  JMG_TRY(solve_llt<float>(c.n, c.nrhs, c.W, c.p->ldw, c.D, c.n, c.sync, &c.ints[2], c.s));
+  return launch_scale_from_f32(c.n, c.nrhs, c.D, c.colmax, Zout, c.s);
+}
+
+// Preconditioned CG on A X = B from the current X and its true residual R,
+// FP64 vectors, M = L L^T (the low-precision factor).  Stops when the
+// recursively updated residual suggests eta <= tol / 2 (the caller then checks
+// the true residual), at maxit, or on a breakdown (p^T A p <= 0).
+static int pcg(MixedCtx& c, bool* breakdown) {
+  const int n = c.n, nrhs = c.nrhs;
+  *breakdown = false;
+  JMG_TRY(precond_to(c, c.Z));
+  JMG_CUDA(cudaMemcpyAsync(c.P, c.Z, sizeof(double) * (size_t)n * nrhs, cudaMemcpyDeviceToDevice,
+                           c.s));
+  JMG_TRY(launch_dot_cols(n, nrhs, c.R, n, c.Z, n, c.rz, c.s));
+  while (c.S->iters < c.o->maxit) {
+    // Q = A P (same FP64 kernel as the residual, without B)
+    JMG_TRY(launch_residual(n, nrhs, c.A, c.lda, c.P, n, nullptr, n, c.Q, n, c.colmax, c.part,
+                            c.p->splits, c.s, c.ev[0], c.ev[1]));
+    JMG_TRY(launch_dot_cols(n, nrhs, c.P, n, c.Q, n, c.pq, c.s));
+    JMG_TRY(launch_pcg_step(n, nrhs, c.P, c.Q, c.rz, c.pq, c.X, c.R, c.colmax, &c.ints[3], c.s));
+    JMG_TRY(launch_eta(nrhs, c.colmax, c.dsc, c.eta, c.s));
+    int bad = 0;
+    JMG_TRY(sync_read(c.eh.data(), c.eta, sizeof(double) * (1 + nrhs), c.s));
+    JMG_TRY(sync_read(&bad, &c.ints[3], sizeof(int), c.s));
+    if (c.o->timing) {
+      float ms = 0.f;
+      JMG_CUDA(cudaEventElapsedTime(&ms, c.ev[0], c.ev[1]));
+      c.S->t_resid_gpu_ms += ms;
+    }
+    c.S->n_resid++;
+    c.S->iters++;
+    hist(c, c.eh[0]);
+    if (bad || std::isnan(c.eh[0])) {
+      *breakdown = true;
+      return JMG_OK;
+    }
+    if (c.eh[0] <= 0.5 * c.o->tol) return JMG_OK;
+    JMG_TRY(precond_to(c, c.Z));
+    JMG_TRY(launch_dot_cols(n, nrhs, c.R, n, c.Z, n, c.rz_new, c.s));
+    JMG_TRY(launch_pcg_dir(n, nrhs, c.Z, c.P, c.rz_new, c.rz, c.s));
+    JMG_CUDA(cudaMemcpyAsync(c.rz, c.rz_new, sizeof(double) * nrhs, cudaMemcpyDeviceToDevice, c.s));
+  }
+  return JMG_OK;
+}
+
 static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int ldb, int* info,
                       const jmg_options& o, jmg_stats* st, void* work, cudaStream_t s) {
   const Plan p = plan_posv_mixed(n, nrhs, o);
-  float* W = at<float>(work, p.off_W);
-  double* X = at<double>(work, p.off_X);
-  double* R = at<double>(work, p.off_R);
-  float* D = at<float>(work, p.off_D);
-  double* part = at<double>(work, p.off_part);
-  double* colmax = at<double>(work, p.off_colmax);
-  double* eta = at<double>(work, p.off_eta);
-  double* anorm = at<double>(work, p.off_anorm);
-  double* rowsum = at<double>(work, p.off_rowsum);
-  int* ints = at<int>(work, p.off_ints);  // [0] info_f, [1] factor err, [2] solve status
   jmg_stats local{};
-  jmg_stats& S = st ? *st : local;
+  MixedCtx c;
+  c.n = n, c.nrhs = nrhs, c.lda = lda, c.ldb = ldb, c.A = A, c.B = B, c.p = &p, c.o = &o;
+  c.work = work, c.s = s;
+  c.W = at<float>(work, p.off_W);
+  c.X = at<double>(work, p.off_X);
+  c.R = at<double>(work, p.off_R);
+  c.Z = at<double>(work, p.off_Z);
+  c.P = at<double>(work, p.off_P);
+  c.Q = at<double>(work, p.off_Q);
+  c.D = at<float>(work, p.off_D);
+  c.part = at<double>(work, p.off_part);
+  c.colmax = at<double>(work, p.off_colmax);
+  c.eta = at<double>(work, p.off_eta);
+  c.dsc = at<double>(work, p.off_anorm);  // [0] ||A||_inf, [1] shift, [2] max_i a_ii
+  c.rowsum = at<double>(work, p.off_rowsum);
+  c.rz = at<double>(work, p.off_scal);
+  c.rz_new = c.rz + nrhs;
+  c.pq = c.rz + 2 * nrhs;
+  c.ints = at<int>(work, p.off_ints);
+  c.sync = at<int>(work, p.off_sync);
+  c.ev[0] = c.ev[1] = nullptr;
+  c.S = st ? st : &local;
+  c.eh.assign(1 + nrhs, 0.0);
+  jmg_stats& S = *c.S;
   S = jmg_stats{};
   S.words_used = o.words;
   S.refine_used = JMG_REFINE_IR;
-
-  double t0 = now_ms();
-  JMG_TRY(launch_norm_inf(n, A, lda, rowsum, anorm, s));
-  double anorm_h = 0;
-  JMG_TRY(sync_read(&anorm_h, anorm, sizeof(double), s));
-  S.anorm = anorm_h;
-
-  // factor, retrying with a diagonal shift when the low-precision factor breaks down
-  double shift = 0.0;
-  int hs[2] = {0, 0};
-  const double u_eff = (o.prec == JMG_PREC_FP16 ? std::ldexp(1.0, -11) : std::ldexp(1.0, -8));
-  const double u_words = std::pow(u_eff, o.words) + std::ldexp(1.0, -24);
-  for (int tries = 0;; ++tries) {
-    JMG_CUDA(cudaMemsetAsync(ints, 0, sizeof(int) * 8, s));
-    JMG_TRY(launch_lower_to_f32(n, A, lda, W, p.ldw, shift, s));
-    JMG_TRY(factor_mixed(n, W, p.ldw, o, p, work, &ints[0], &ints[1], s));
-    JMG_TRY(sync_read(hs, ints, sizeof(int) * 2, s));
-    S.factor_tries = tries + 1;
-    if (hs[1]) return S.status = JMG_ERR_TIMEOUT;
-    if (hs[0] == 0) break;
-    if (!o.shift_retry || tries >= 4) {
-      JMG_CUDA(cudaMemcpyAsync(info, &ints[0], sizeof(int), cudaMemcpyDeviceToDevice, s));
-      S.info = hs[0];
-      return S.status = JMG_ERR_NOT_SPD;
-    }
-    shift = (shift == 0.0) ? 4.0 * u_words * anorm_h : shift * 8.0;
-  }
-  S.shift = shift;
-  JMG_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
-  double t1 = now_ms();
-  S.t_factor_ms = t1 - t0;
-
-  // initial solve X = M^{-1} B
-  JMG_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)n * nrhs, s));
-  JMG_CUDA(cudaMemsetAsync(colmax, 0, sizeof(double) * 3 * nrhs, s));
-  {
-    dim3 grid(std::min(cdiv(n, 256), 64), nrhs);
-    k_copy_colmax<<<grid, 256, 0, s>>>(n, B, ldb, R, colmax);
-    JMG_TRY(launched());
-  }
-  JMG_TRY(precond_update(n, nrhs, W, p.ldw, R, colmax, D, X, at<int>(work, p.off_sync), &ints[2],
-                           s));
-  double t2 = now_ms();
-
-  // FP64 iterative refinement
-  std::vector<double> eh(1 + nrhs);
-  double prev = INFINITY;
-  int stall = 0;
-  int it = 0;
-  cudaEvent_t ev[2] = {nullptr, nullptr};
   if (o.timing) {
-    JMG_CUDA(cudaEventCreate(&ev[0]));
-    JMG_CUDA(cudaEventCreate(&ev[1]));
+    JMG_CUDA(cudaEventCreate(&c.ev[0]));
+    JMG_CUDA(cudaEventCreate(&c.ev[1]));
   }
-  for (;; ++it) {
-    JMG_TRY(launch_residual(n, nrhs, A, lda, X, n, B, ldb, R, n, colmax, part, p.splits, s, ev[0],
-                            ev[1]));
-    JMG_TRY(launch_eta(nrhs, colmax, anorm, eta, s));
-    JMG_TRY(sync_read(eh.data(), eta, sizeof(double) * (1 + nrhs), s));
-    S.n_resid++;
-    if (o.timing) {
-      float ms = 0.f;
-      JMG_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
-      S.t_resid_gpu_ms += ms;
+  struct EvGuard {
+    cudaEvent_t* e;
+    ~EvGuard() {
+      if (e[0]) cudaEventDestroy(e[0]);
+      if (e[1]) cudaEventDestroy(e[1]);
     }
-    S.bwd_err = eh[0];
-    if (eh[0] <= o.tol) break;
-    if (it >= o.maxit || std::isnan(eh[0])) {
-      S.status = JMG_ERR_NOT_CONVERGED;
-      break;
-    }
-    stall = (eh[0] > 0.5 * prev) ? stall + 1 : 0;
-    if (stall >= 3) {
-      S.status = JMG_ERR_NOT_CONVERGED;
-      break;
-    }
-    prev = eh[0];
-    JMG_TRY(precond_update(n, nrhs, W, p.ldw, R, colmax, D, X, at<int>(work, p.off_sync), &ints[2],
-                           s));
+  } guard{c.ev};
+
+  const double t0 = now_ms();
+  if (!o.reuse_factor) {
+    JMG_TRY(launch_norm_inf(n, A, lda, c.rowsum, &c.dsc[0], s));
+    JMG_TRY(launch_diag_max(n, A, lda, &c.dsc[2], s));
+    JMG_CUDA(cudaMemsetAsync(&c.dsc[1], 0, sizeof(double), s));
   }
-  S.iters = it;
+  double h3[3] = {0, 0, 0};
+  JMG_TRY(sync_read(h3, c.dsc, sizeof(h3), s));
+  S.anorm = h3[0];
+  double shift = h3[1];
+  const double dmax = h3[2];
+  // unit roundoff of the factor: the split words, but never below FP32's
+  const double u_f = std::max(std::pow(o.prec == JMG_PREC_FP16 ? std::ldexp(1.0, -11)
+                                                               : std::ldexp(1.0, -8),
+                                       o.words),
+                              std::ldexp(1.0, -24));
+  auto next_shift = [&](double sh) { return sh == 0.0 ? 4.0 * u_f * dmax : 16.0 * sh; };
+
+  bool converged = false;
+  for (int attempt = 0;; ++attempt) {
+    if (!o.reuse_factor || attempt > 0) {
+      for (;;) {  // factor, shifting the diagonal while the low-precision factor breaks down
+        JMG_CUDA(cudaMemsetAsync(c.ints, 0, sizeof(int) * 4, s));
+        JMG_TRY(launch_lower_to_f32(n, A, lda, c.W, p.ldw, shift, s));
+        JMG_TRY(factor_mixed(n, c.W, p.ldw, o, p, work, &c.ints[0], &c.ints[1], s));
+        int hs[2] = {0, 0};
+        JMG_TRY(sync_read(hs, c.ints, sizeof(hs), s));
+        S.factor_tries++;
+        if (hs[1]) return S.status = JMG_ERR_TIMEOUT;
+        if (hs[0] == 0) break;
+        if (!o.shift_retry || S.factor_tries >= 6) {
+          JMG_CUDA(cudaMemcpyAsync(info, &c.ints[0], sizeof(int), cudaMemcpyDeviceToDevice, s));
+          S.info = hs[0];
+          return S.status = JMG_ERR_NOT_SPD;
+        }
+        shift = next_shift(shift);
+      }
+      JMG_CUDA(cudaMemcpyAsync(&c.dsc[1], &shift, sizeof(double), cudaMemcpyHostToDevice, s));
+      JMG_CUDA(cudaStreamSynchronize(s));
+    } else {
+      JMG_CUDA(cudaMemsetAsync(&c.ints[2], 0, sizeof(int) * 2, s));
+    }
+    S.shift = shift;
+    const double t1 = now_ms();
+    S.t_factor_ms += t1 - t0;
+
+    // initial solve X = M^{-1} B
+    JMG_CUDA(cudaMemsetAsync(c.X, 0, sizeof(double) * (size_t)n * nrhs, s));
+    JMG_CUDA(cudaMemsetAsync(c.colmax, 0, sizeof(double) * 3 * nrhs, s));
+    {
+      dim3 grid(std::min(cdiv(n, 256), 64), nrhs);
+      k_copy_colmax<<<grid, 256, 0, s>>>(n, B, ldb, c.R, c.colmax);
+      JMG_TRY(launched());
+    }
+    JMG_TRY(precond_update(n, nrhs, c.W, p.ldw, c.R, c.colmax, c.D, c.X, c.sync, &c.ints[2], s));
+    const double t2 = now_ms();
+    S.t_solve_ms += t2 - t1;
+
+    // refinement: classic IR, switching to PCG when IR is slow or diverges
+    bool use_pcg = (o.refine == JMG_REFINE_PCG);
+    double prev = INFINITY;
+    int stall = 0;
+    bool breakdown = false;
+    for (;;) {
+      JMG_TRY(true_residual(c));
+      hist(c, c.eh[0]);
+      S.bwd_err = c.eh[0];
+      if (c.eh[0] <= o.tol) {
+        converged = true;
+        break;
+      }
+      if (S.iters >= o.maxit || std::isnan(c.eh[0])) break;
+      if (!use_pcg) {
+        const bool slow = S.iters >= 1 && c.eh[0] > 0.25 * prev;
+        if (o.refine == JMG_REFINE_AUTO && slow) {
+          use_pcg = true;
+        } else if (o.refine == JMG_REFINE_IR) {
+          stall = (c.eh[0] > 0.5 * prev) ? stall + 1 : 0;
+          if (stall >= 3) break;
+        }
+      }
+      prev = c.eh[0];
+      if (!use_pcg) {
+        JMG_TRY(precond_update(n, nrhs, c.W, p.ldw, c.R, c.colmax, c.D, c.X, c.sync, &c.ints[2],
+                               s));
+        S.iters++;
+        continue;
+      }
+      S.refine_used = JMG_REFINE_PCG;
+      JMG_TRY(pcg(c, &breakdown));
+      if (breakdown) break;
+    }
+    S.t_refine_ms += now_ms() - t2;
+    if (converged) break;
+    // not converged: refactor with a (larger) diagonal shift
+    if (!o.shift_retry || attempt >= 3 || S.iters >= o.maxit) break;
+    shift = next_shift(shift);
+  }
   {
     int hs3[3] = {0, 0, 0};
-    JMG_TRY(sync_read(hs3, ints, sizeof(int) * 3, s));
-    if (hs3[2] != 0) S.status = JMG_ERR_TIMEOUT;
+    JMG_TRY(sync_read(hs3, c.ints, sizeof(hs3), s));
+    if (hs3[2] != 0) return S.status = JMG_ERR_TIMEOUT;
   }
-  if (o.timing) {
-    cudaEventDestroy(ev[0]);
-    cudaEventDestroy(ev[1]);
-  }
-  JMG_TRY(launch_copy2d(n, nrhs, X, n, B, ldb, s));
+  JMG_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
+  JMG_TRY(launch_copy2d(n, nrhs, c.X, n, B, ldb, s));
   JMG_CUDA(cudaStreamSynchronize(s));
-  double t3 = now_ms();
-  S.t_solve_ms = t2 - t1;
-  S.t_refine_ms = t3 - t2;
+  S.status = converged ? JMG_OK : JMG_ERR_NOT_CONVERGED;
   return S.status;
 }
 
@@ -302,10 +429,11 @@ void jmg_default_options(jmg_options* o) {
   o->prec = JMG_PREC_NATIVE;
   o->words = 1;
   o->tol = 1e-13;
-  o->maxit = 30;
+  o->maxit = 50;
   o->refine = JMG_REFINE_AUTO;
   o->shift_retry = 1;
   o->timing = 0;
+  o->reuse_factor = 0;
 }
 
 size_t jmg_workspace_size(int op, int n, int nrhs, int dtype, const jmg_options* opt) {
@@ -426,6 +554,18 @@ int jmg_logdet(int n, const void* L, int lda, int dtype, double* out, void* stre
 }
 
 // ---------------------------------------------------------------- dev entry points
+int jmg_sym_grad(int n, int nrhs, const double* Bbar, int ldb, const double* X, int ldx,
+                 double* Abar, int ldab, void* stream) {
+  if (n < 0) return -1;
+  if (nrhs < 0) return -2;
+  if (ldb < std::max(1, n)) return -4;
+  if (ldx < std::max(1, n)) return -6;
+  if (ldab < std::max(1, n)) return -8;
+  if (n > 0 && !Abar) return -7;
+  if (n > 0 && nrhs > 0 && (!Bbar || !X)) return !Bbar ? -3 : -5;
+  return launch_sym_grad(n, nrhs, Bbar, ldb, X, ldx, Abar, ldab, (cudaStream_t)stream);
+}
+
 int jmg_dev_syrk_tc(int m, int ncols, int kext, const void* PA, const void* PB, int ldp,
                     int prec, float* C, int ldc, int* err, void* stream) {
   if (m < 0) return -1;

@@ -583,8 +583,9 @@ __global__ void k_resid_reduce(int n, int nrhs, int splits, const double* __rest
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double acc = 0.0;
     for (int z = 0; z < splits; ++z) acc += part[(size_t)z * n * nrhs + (size_t)c * n + i];
-    double b = B[(size_t)c * ldb + i];
-    double r = b - acc;
+    // B == nullptr: plain product (PCG's Q = A P) instead of the residual
+    double b = B ? B[(size_t)c * ldb + i] : 0.0;
+    double r = B ? b - acc : acc;
     R[(size_t)c * ldr + i] = r;
     double x = X[(size_t)c * ldx + i];
     rm = (isnan(r) || isnan(rm)) ? NAN : fmax(rm, fabs(r));
@@ -846,6 +847,138 @@ int launch_copy2d(int n, int nrhs, const double* src, int lds, double* dst, int 
 int launch_zero(double* p, size_t n, cudaStream_t s) {
   JMG_CUDA(cudaMemsetAsync(p, 0, sizeof(double) * n, s));
   return JMG_OK;
+}
+
+}  // namespace jmg
+
+namespace jmg {
+
+// ============================================================================
+// Vector kernels of the preconditioned conjugate gradient refinement (FP64,
+// one right-hand side per column, columns independent).
+// ============================================================================
+
+// out[c] = sum_i U[i,c] V[i,c]; one CTA per column, fixed reduction order.
+__global__ void __launch_bounds__(256) k_dot_cols(int n, const double* __restrict__ U, int ldu,
+                                                  const double* __restrict__ V, int ldv,
+                                                  double* __restrict__ out) {
+  __shared__ double part[256];
+  const int c = blockIdx.x;
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) a = fma(U[(size_t)c * ldu + i], V[(size_t)c * ldv + i], a);
+  part[threadIdx.x] = a;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = part[0];
+}
+
+int launch_dot_cols(int n, int nrhs, const double* U, int ldu, const double* V, int ldv,
+                    double* out, cudaStream_t s) {
+  k_dot_cols<<<nrhs, 256, 0, s>>>(n, U, ldu, V, ldv, out);
+  return launched();
+}
+
+// alpha_c = rz_c / pq_c (0 when pq_c <= 0, which also raises *bad);
+// X += alpha P, R -= alpha Q; colmax[0..nrhs) = ||R||, [nrhs..2nrhs) = ||X||.
+__global__ void k_pcg_step(int n, const double* __restrict__ P, const double* __restrict__ Q,
+                           const double* __restrict__ rz, const double* __restrict__ pq,
+                           double* __restrict__ X, double* __restrict__ R, int nrhs,
+                           double* __restrict__ colmax, int* __restrict__ bad) {
+  const int c = blockIdx.y;
+  const double den = pq[c];
+  double alpha = 0.0;
+  if (den > 0.0 && isfinite(den)) {
+    alpha = rz[c] / den;
+  } else if (rz[c] != 0.0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(bad, 1);
+  }
+  double rm = 0.0, xm = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const size_t o = (size_t)c * n + i;
+    const double x = fma(alpha, P[o], X[o]);
+    const double r = fma(-alpha, Q[o], R[o]);
+    X[o] = x;
+    R[o] = r;
+    rm = (isnan(r) || isnan(rm)) ? NAN : fmax(rm, fabs(r));
+    xm = (isnan(x) || isnan(xm)) ? NAN : fmax(xm, fabs(x));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    double a = __shfl_xor_sync(0xffffffffu, rm, o);
+    rm = (isnan(a) || isnan(rm)) ? NAN : fmax(rm, a);
+    a = __shfl_xor_sync(0xffffffffu, xm, o);
+    xm = (isnan(a) || isnan(xm)) ? NAN : fmax(xm, a);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg(&colmax[c], rm);
+    atomic_max_nonneg(&colmax[nrhs + c], xm);
+  }
+}
+
+int launch_pcg_step(int n, int nrhs, const double* P, const double* Q, const double* rz,
+                    const double* pq, double* X, double* R, double* colmax, int* bad,
+                    cudaStream_t s) {
+  JMG_CUDA(cudaMemsetAsync(colmax, 0, sizeof(double) * 2 * nrhs, s));
+  dim3 grid(std::min(cdiv(n, 256), 64), nrhs);
+  k_pcg_step<<<grid, 256, 0, s>>>(n, P, Q, rz, pq, X, R, nrhs, colmax, bad);
+  return launched();
+}
+
+// P = Z + (rz_new / rz_old) P   (beta = 0 when rz_old == 0); then rz_old = rz_new
+__global__ void k_pcg_dir(int n, const double* __restrict__ Z, double* __restrict__ P,
+                          const double* __restrict__ rz_new, const double* __restrict__ rz_old) {
+  const int c = blockIdx.y;
+  const double beta = (rz_old[c] != 0.0) ? rz_new[c] / rz_old[c] : 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const size_t o = (size_t)c * n + i;
+    P[o] = fma(beta, P[o], Z[o]);
+  }
+}
+
+int launch_pcg_dir(int n, int nrhs, const double* Z, double* P, const double* rz_new,
+                   const double* rz_old, cudaStream_t s) {
+  dim3 grid(std::min(cdiv(n, 256), 64), nrhs);
+  k_pcg_dir<<<grid, 256, 0, s>>>(n, Z, P, rz_new, rz_old);
+  return launched();
+}
+
+// Z = scale_c * D32 (FP64 from the FP32 preconditioner output)
+__global__ void k_scale_from_f32(int n, const float* __restrict__ D, const double* __restrict__ colmax_r,
+                                 double* __restrict__ Z) {
+  const int c = blockIdx.y;
+  double sc = colmax_r[c];
+  if (!(sc > 0.0 && isfinite(sc))) sc = 1.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    Z[(size_t)c * n + i] = sc * (double)D[(size_t)c * n + i];
+}
+
+int launch_scale_from_f32(int n, int nrhs, const float* D, const double* colmax_r, double* Z,
+                          cudaStream_t s) {
+  dim3 grid(std::min(cdiv(n, 256), 64), nrhs);
+  k_scale_from_f32<<<grid, 256, 0, s>>>(n, D, colmax_r, Z);
+  return launched();
+}
+
+// max_i A_ii (A_ii > 0 expected; NaN wins) into *out (must be zeroed)
+__global__ void k_diag_max(int n, const double* __restrict__ A, int lda, double* __restrict__ out) {
+  double m = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double v = A[(size_t)i * lda + i];
+    m = (isnan(v) || isnan(m)) ? NAN : fmax(m, fabs(v));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double a = __shfl_xor_sync(0xffffffffu, m, o);
+    m = (isnan(a) || isnan(m)) ? NAN : fmax(m, a);
+  }
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
+}
+
+int launch_diag_max(int n, const double* A, int lda, double* out, cudaStream_t s) {
+  JMG_CUDA(cudaMemsetAsync(out, 0, sizeof(double), s));
+  k_diag_max<<<std::max(1, std::min(cdiv(n, 256), 64)), 256, 0, s>>>(n, A, lda, out);
+  return launched();
 }
 
 }  // namespace jmg

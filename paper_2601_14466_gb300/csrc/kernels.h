@@ -1,6 +1,8 @@
 // kernels.h -- internal launchers of the SPD solver's kernels (not exported).
 #pragma once
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace jmg {
@@ -97,6 +99,22 @@ int launch_copy2d(int n, int nrhs, const double* src, int lds, double* dst, int 
                   cudaStream_t s);
 // clear n doubles
 int launch_zero(double* p, size_t n, cudaStream_t s);
+
+// ---- preconditioned CG (FP64, columns independent)
+int launch_dot_cols(int n, int nrhs, const double* U, int ldu, const double* V, int ldv,
+                    double* out, cudaStream_t s);
+int launch_pcg_step(int n, int nrhs, const double* P, const double* Q, const double* rz,
+                    const double* pq, double* X, double* R, double* colmax, int* bad,
+                    cudaStream_t s);
+int launch_pcg_dir(int n, int nrhs, const double* Z, double* P, const double* rz_new,
+                   const double* rz_old, cudaStream_t s);
+int launch_scale_from_f32(int n, int nrhs, const float* D, const double* colmax_r, double* Z,
+                          cudaStream_t s);
+int launch_diag_max(int n, const double* A, int lda, double* out, cudaStream_t s);
+
+// ---- adjoint (k_grad.cu): G = -(Bb X^T + X Bb^T)/2, full symmetric n x n
+int launch_sym_grad(int n, int nrhs, const double* Bb, int ldb, const double* X, int ldx, double* G,
+                    int ldg, cudaStream_t s);
 
 // ---- tensor-core trailing update (k_tc.cu)
 // C (m x ncols, lower trapezoid: rows >= columns) -= PA PB^T, PA/PB: m x kext

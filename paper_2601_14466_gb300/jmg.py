@@ -46,7 +46,8 @@ class JmgError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int), ("NB", ctypes.c_int), ("prec", ctypes.c_int),
                 ("words", ctypes.c_int), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
-                ("refine", ctypes.c_int), ("shift_retry", ctypes.c_int), ("timing", ctypes.c_int)]
+                ("refine", ctypes.c_int), ("shift_retry", ctypes.c_int), ("timing", ctypes.c_int),
+                ("reuse_factor", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -56,7 +57,8 @@ class Stats(ctypes.Structure):
                 ("shift", ctypes.c_double), ("anorm", ctypes.c_double),
                 ("t_factor_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
                 ("t_refine_ms", ctypes.c_double), ("t_resid_gpu_ms", ctypes.c_double),
-                ("n_resid", ctypes.c_int)]
+                ("n_resid", ctypes.c_int), ("n_hist", ctypes.c_int),
+                ("eta_hist", ctypes.c_double * 32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -75,6 +77,7 @@ _SIGS = {
                       ctypes.POINTER(Stats), _P, _SZ, _P]),
     "jmg_logdet": (_I, [_I, _P, _I, _I, _P, _P]),
     "jmg_status_string": (ctypes.c_char_p, [_I]),
+    "jmg_sym_grad": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P]),
     "jmg_dev_syrk_tc": (_I, [_I, _I, _I, _P, _P, _I, _I, _P, _I, _P, _P]),
     "jmg_dev_syrk_fp8": (_I, [_I, _I, _P, _I, _P, _P, _I, _P, _P]),
     "jmg_dev_residual_workspace": (_SZ, [_I, _I]),
@@ -217,12 +220,13 @@ class SolveInfo:
     refine_used: int
     t_resid_gpu_ms: float = 0.0
     n_resid: int = 0
+    eta_hist: tuple = ()
 
 
 def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1, nb: int = 128,
-         tol: float = 1e-13, maxit: int = 30, refine: str = "auto", shift_retry: bool = True,
+         tol: float = 1e-13, maxit: int = 50, refine: str = "auto", shift_retry: bool = True,
          overwrite_a: bool = False, work: torch.Tensor | None = None, check: bool = True,
-         timing: bool = False):
+         timing: bool = False, reuse_factor: bool = False):
     """Solve A X = B for SPD A (lower triangle of the column-major A read).
 
     prec "fp64": potrf + potrs in FP64 (A is overwritten with L only when
@@ -238,7 +242,8 @@ def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1
     n, nrhs = A.shape[0], B.shape[1]
     X = colmajor_copy(B)
     o = default_options(nb=nb, prec=prec, words=words, tol=tol, maxit=maxit, refine=refine,
-                        shift_retry=int(shift_retry), timing=int(timing))
+                        shift_retry=int(shift_retry), timing=int(timing),
+                        reuse_factor=int(reuse_factor))
     Aw = A if (overwrite_a or o.prec != 0) else colmajor_copy(A)
     pa, lda = _colmajor(Aw, "A")
     px, ldx = _colmajor(X, "B")
@@ -258,10 +263,24 @@ def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1
         si = SolveInfo(stats.status, stats.info, stats.iters, stats.bwd_err, stats.shift,
                        stats.words_used, stats.factor_tries, stats.anorm, stats.t_factor_ms,
                        stats.t_solve_ms, stats.t_refine_ms, stats.refine_used,
-                       stats.t_resid_gpu_ms, stats.n_resid)
+                       stats.t_resid_gpu_ms, stats.n_resid,
+                       tuple(stats.eta_hist[i] for i in range(min(stats.n_hist, 32))))
         if check and st != 0:
             raise JmgError(st, "jmg_posv")
     return (X[:, 0] if squeeze else X), si
+
+
+def sym_grad(Bbar: torch.Tensor, X: torch.Tensor) -> torch.Tensor:
+    """Abar = -(Bbar X^T + X Bbar^T) / 2 as a new n x n FP64 tensor (symmetric, so
+    its row- and column-major forms coincide)."""
+    _need_cuda(Bbar, X)
+    pb, ldb = _colmajor(Bbar, "Bbar")
+    px, ldx = _colmajor(X, "X")
+    n, nrhs = X.shape
+    G = torch.empty((n, n), dtype=torch.float64, device=X.device)
+    _chk(load().jmg_sym_grad(n, nrhs, pb, ldb, px, ldx, G.data_ptr(), max(n, 1), _stream(X.device)),
+         "jmg_sym_grad")
+    return G
 
 
 def logdet(L: torch.Tensor) -> torch.Tensor:

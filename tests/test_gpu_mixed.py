@@ -76,6 +76,39 @@ def test_posv_leaves_inputs_alone(prec):
     assert torch.allclose(X, X2, rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("refine", ["pcg", "auto"])
+@pytest.mark.parametrize("kappa,prec,words", [(1e6, "bf16", 3), (1e8, "bf16", 3), (1e8, "fp16", 2)])
+def test_posv_mixed_high_kappa(kappa, prec, words, refine):
+    # kappa * u_factor >= 1: stationary refinement alone stalls; PCG preconditioned
+    # by the (possibly diagonally shifted) factor must still reach 1e-13
+    n, nrhs = 1000, 3
+    A = inputs.q_lambda(n, kappa, seed=inputs.seed_for("hk", kappa))
+    Xt = inputs.uniform(n, nrhs, seed=7)
+    B = inputs.rhs_from(A, Xt)
+    Ad, _ = to_dev_colmajor(lower_only(A))
+    Bd, _ = to_dev_colmajor(B)
+    X, si = jmg.posv(Ad, Bd, prec=prec, words=words, refine=refine, maxit=200)
+    assert si.status == 0, si
+    _check(A, B, X, kappa)
+
+
+def test_posv_reuse_factor():
+    # a refine-only call with the factor left in the workspace by a first call
+    n, nrhs = 700, 3
+    A = inputs.gram_shift(n, 1e-2, seed=41)
+    B1 = inputs.uniform(n, nrhs, seed=42)
+    B2 = inputs.normal(n, nrhs + 2, seed=43)
+    Ad, _ = to_dev_colmajor(A)
+    work = jmg.workspace(jmg.OP_POSV, n, nrhs + 2, jmg.default_options(prec="bf16", words=2),
+                         "cuda")
+    X1, s1 = jmg.posv(Ad, to_dev_colmajor(B1)[0], prec="bf16", words=2, work=work)
+    X2, s2 = jmg.posv(Ad, to_dev_colmajor(B2)[0], prec="bf16", words=2, work=work,
+                      reuse_factor=True)
+    assert s1.factor_tries == 1 and s2.factor_tries == 0
+    _check(A, B1, X1, kappa=500.0)
+    _check(A, B2, X2, kappa=500.0)
+
+
 def test_posv_mixed_not_spd():
     n = 300
     A = inputs.gram_shift(n, 1.0, seed=2)
