@@ -29,12 +29,14 @@ int jmg_dev_syrk_tc(int m, int ncols, int kext, const void* PA, const void* PB, 
                     int prec, float* C, int ldc, int* err, void* stream);
 
 /*
- * FP8 (e4m3) variant with one power-of-two scale per 128 x 128 tile:
- *     C[i, j] -= sum_c 2^-(e[i/128, c] + e[j/128, c]) * sum_{k in chunk c} Q[i, k] Q[j, k]
- * Q: m x kext e4m3 bytes, row-major, ldq bytes (multiple of 128); e: int8
- * exponents, row-major [ceil(m/128)] x [kext/128].  C as above.
+ * FP8 (e4m3) variant with one power-of-two scale per 128-row tile of the panel
+ * (with a 128-wide panel, kext = 128, that is one scale per 128 x 128 tile):
+ *     C[i, j] -= 2^-(e[i/128] + e[j/128]) * sum_k Q[i, k] Q[j, k]
+ *         for 0 <= j <= i < m, j < ncols
+ * Q: m x kext e4m3 bytes, row-major, ldq bytes (kext, ldq multiples of 128;
+ * 16-byte aligned); e: ceil(m/128) int8 exponents.  C, err as above.
  */
-int jmg_dev_syrk_fp8(int m, int kext, const void* Q, int ldq, const signed char* e,
+int jmg_dev_syrk_fp8(int m, int ncols, int kext, const void* Q, int ldq, const signed char* e,
                      float* C, int ldc, int* err, void* stream);
 
 /*

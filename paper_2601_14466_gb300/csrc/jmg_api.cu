@@ -25,7 +25,7 @@ namespace jmg {
 struct Plan {
   size_t off_W = 0, off_PA = 0, off_PB = 0, off_X = 0, off_R = 0, off_D = 0, off_part = 0,
          off_colmax = 0, off_eta = 0, off_anorm = 0, off_rowsum = 0, off_ints = 0, off_Z = 0,
-         off_P = 0, off_Q = 0, off_scal = 0, off_sync = 0, total = 0;
+         off_P = 0, off_Q = 0, off_scal = 0, off_sync = 0, off_exp = 0, total = 0;
   int ldw = 0, ldp = 0, kext = 0, splits = 1;
 };
 
@@ -52,7 +52,7 @@ static Plan plan_posv_mixed(int n, int nrhs, const jmg_options& o) {
   };
   const size_t N = (size_t)n, R = (size_t)(nrhs > 0 ? nrhs : 1);
   p.ldw = (int)round_up(N > 0 ? N : 1, 32);
-  p.kext = o.nb * split_pairs(o.words);
+  p.kext = o.prec == JMG_PREC_FP8 ? o.nb : o.nb * split_pairs(o.words);
   p.ldp = (int)round_up((size_t)p.kext, 64);
   p.splits = residual_splits(n, nrhs > 0 ? nrhs : 1);
   // the factor and what a refine-only call (reuse_factor) needs come first, at
@@ -60,7 +60,8 @@ static Plan plan_posv_mixed(int n, int nrhs, const jmg_options& o) {
   p.off_W = take(sizeof(float) * (size_t)p.ldw * N);
   p.off_anorm = take(sizeof(double) * 2);  // [0] ||A||_inf, [1] shift of the factor
   p.off_ints = take(sizeof(int) * 8);
-  p.off_PA = take(2 * N * p.ldp);
+  p.off_PA = take(2 * N * p.ldp);  // 16-bit words, or e4m3 bytes for FP8
+  p.off_exp = take(N / 128 + 2);
   p.off_PB = take(2 * N * p.ldp);
   p.off_X = take(sizeof(double) * N * R);
   p.off_R = take(sizeof(double) * N * R);
@@ -122,9 +123,16 @@ static int factor_mixed(int n, float* W, int ldw, const jmg_options& o, const Pl
     if (m <= 0) break;
     float* L21 = Wkk + kb;
     JMG_TRY(launch_trsm(L21, ldw, m, kb, Wkk, info_f, s));
-    JMG_TRY(launch_split_words(m, kb, L21, ldw, o.prec, o.words, PA, PB, p.ldp, s));
-    JMG_TRY(launch_syrk_tc(m, m, kb * split_pairs(o.words), PA, PB, p.ldp, o.prec,
-                           W + (size_t)(k + kb) * ldw + (k + kb), ldw, err, s));
+    float* W22 = W + (size_t)(k + kb) * ldw + (k + kb);
+    if (o.prec == JMG_PREC_FP8) {
+      signed char* ex = at<signed char>(work, p.off_exp);
+      JMG_TRY(launch_quant_fp8(m, kb, L21, ldw, PA, p.ldp, ex, s));
+      JMG_TRY(launch_syrk_fp8(m, m, kb, PA, p.ldp, ex, W22, ldw, err, s));
+    } else {
+      JMG_TRY(launch_split_words(m, kb, L21, ldw, o.prec, o.words, PA, PB, p.ldp, s));
+      JMG_TRY(launch_syrk_tc(m, m, kb * split_pairs(o.words), PA, PB, p.ldp, o.prec, W22, ldw,
+                             err, s));
+    }
   }
   return JMG_OK;
 }
@@ -311,10 +319,12 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
   double shift = h3[1];
   const double dmax = h3[2];
   // unit roundoff of the factor: the split words, but never below FP32's
-  const double u_f = std::max(std::pow(o.prec == JMG_PREC_FP16 ? std::ldexp(1.0, -11)
-                                                               : std::ldexp(1.0, -8),
-                                       o.words),
-                              std::ldexp(1.0, -24));
+  const double u_f =
+      o.prec == JMG_PREC_FP8
+          ? std::ldexp(1.0, -4)
+          : std::max(std::pow(o.prec == JMG_PREC_FP16 ? std::ldexp(1.0, -11) : std::ldexp(1.0, -8),
+                              o.words),
+                     std::ldexp(1.0, -24));
   auto next_shift = [&](double sh) { return sh == 0.0 ? 4.0 * u_f * dmax : 16.0 * sh; };
 
   bool converged = false;
@@ -521,7 +531,9 @@ int jmg_posv(int n, int nrhs, void* A, int lda, void* B, int ldb, int dtype, int
                                 s));
     return JMG_OK;
   }
-  if (o.prec != JMG_PREC_BF16 && o.prec != JMG_PREC_FP16) return JMG_ERR_UNSUPPORTED;
+  if (o.prec != JMG_PREC_BF16 && o.prec != JMG_PREC_FP16 && o.prec != JMG_PREC_FP8)
+    return JMG_ERR_UNSUPPORTED;
+  if (o.prec == JMG_PREC_FP8 && o.nb != 128) return -9;
   if (nrhs == 0) return JMG_OK;
   size_t need = plan_posv_mixed(n, nrhs, o).total;
   if (!work || lwork < need) return JMG_ERR_WORKSPACE;
@@ -575,12 +587,13 @@ int jmg_dev_syrk_tc(int m, int ncols, int kext, const void* PA, const void* PB, 
   return launch_syrk_tc(m, ncols, kext, PA, PB, ldp, prec, C, ldc, err, (cudaStream_t)stream);
 }
 
-int jmg_dev_syrk_fp8(int m, int kext, const void* Q, int ldq, const signed char* e, float* C,
-                     int ldc, int* err, void* stream) {
+int jmg_dev_syrk_fp8(int m, int ncols, int kext, const void* Q, int ldq, const signed char* e,
+                     float* C, int ldc, int* err, void* stream) {
   if (m < 0) return -1;
-  if (ldc < std::max(1, m)) return -7;
-  if (!err) return -8;
-  return launch_syrk_fp8(m, kext, Q, ldq, e, C, ldc, err, (cudaStream_t)stream);
+  if (ncols < 0 || ncols > m) return -2;
+  if (ldc < std::max(1, m)) return -8;
+  if (!err) return -9;
+  return launch_syrk_fp8(m, ncols, kext, Q, ldq, e, C, ldc, err, (cudaStream_t)stream);
 }
 
 size_t jmg_dev_residual_workspace(int n, int nrhs) {

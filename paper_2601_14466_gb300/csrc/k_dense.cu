@@ -982,3 +982,61 @@ int launch_diag_max(int n, const double* A, int lda, double* out, cudaStream_t s
 }
 
 }  // namespace jmg
+
+#include <cuda_fp8.h>
+
+namespace jmg {
+
+// ============================================================================
+// FP8 quantisation of the panel with one power-of-two scale per 128-row tile
+// (the 128 x 128 tiles of a 128-wide panel): one CTA per tile finds amax,
+// picks e = floor(log2(448 / amax)) (448 = largest finite e4m3) clamped to
+// [-126, 126], and writes q = e4m3_rn_satfinite(x * 2^e) row-major.
+// ============================================================================
+__global__ void __launch_bounds__(256) k_quant_fp8(int m, int kb, const float* __restrict__ L21,
+                                                   int ldw, unsigned char* __restrict__ Q, int ldq,
+                                                   signed char* __restrict__ ex) {
+  __shared__ float red[8];
+  __shared__ int s_e;
+  const int r0 = blockIdx.x * 128;
+  const int rows = min(128, m - r0);
+  const int t = threadIdx.x;
+  float amax = 0.0f;
+  for (int idx = t; idx < rows * kb; idx += 256) {
+    const int i = idx % rows, c = idx / rows;
+    amax = fmaxf(amax, fabsf(L21[(size_t)c * ldw + r0 + i]));
+  }
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if ((t & 31) == 0) red[t / 32] = amax;
+  __syncthreads();
+  if (t == 0) {
+    float a = red[0];
+    for (int w = 1; w < 8; ++w) a = fmaxf(a, red[w]);
+    int e = 0;
+    if (a > 0.0f && isfinite(a)) {
+      e = (int)floorf(log2f(448.0f / a));
+      // guard the rounding of log2f: keep a * 2^e <= 448
+      while (e > -126 && ldexpf(a, e) > 448.0f) --e;
+      e = max(-126, min(126, e));
+    }
+    s_e = e;
+    ex[blockIdx.x] = (signed char)e;
+  }
+  __syncthreads();
+  const int e = s_e;
+  // write row-major: consecutive threads take consecutive columns of a row
+  for (int idx = t; idx < rows * kb; idx += 256) {
+    const int c = idx % kb, i = idx / kb;
+    const float v = ldexpf(L21[(size_t)c * ldw + r0 + i], e);
+    Q[(size_t)(r0 + i) * ldq + c] = (unsigned char)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+  }
+}
+
+int launch_quant_fp8(int m, int kb, const float* L21, int ldw, void* Q, int ldq, signed char* e,
+                     cudaStream_t s) {
+  if (m <= 0) return JMG_OK;
+  k_quant_fp8<<<cdiv(m, 128), 256, 0, s>>>(m, kb, L21, ldw, (unsigned char*)Q, ldq, e);
+  return launched();
+}
+
+}  // namespace jmg

@@ -103,6 +103,15 @@ JMG_DEV void tc_mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+JMG_DEV void tc_mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 JMG_DEV void tc_commit(uint64_t* bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -170,10 +179,17 @@ constexpr int PTHREADS = 192;
 constexpr int PSMEM_BYTES = PSTAGES * STAGE_BYTES + 1024 + 512;
 constexpr uint32_t PTMEM_COLS = 256;
 
+// KIND 0: kind::f16 (BF16 / FP16 words, 64 elements = 128 bytes per stage row,
+//         K = 16 per instruction); ab_fmt selects BF16 (1) or FP16 (0).
+// KIND 1: kind::f8f6f4 with E4M3 operands (128 elements per stage row, K = 32
+//         per instruction); the accumulator of tile (ti, tj) is scaled by
+//         2^-(exps[ti] + exps[tj]) in the epilogue (power-of-two tile scales).
+// Both step 32 bytes along the swizzled row per instruction.
+template <int KIND>
 __global__ void __launch_bounds__(PTHREADS, 1)
     k_syrk_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               float* __restrict__ C, int ldc, int m, int ncols, int kext, int ab_fmt,
-              int ntiles, int TJ, int* __restrict__ err) {
+              int ntiles, int TJ, const signed char* __restrict__ exps, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char sm_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(sm_raw) + 1023) & ~uintptr_t(1023));
@@ -185,7 +201,7 @@ __global__ void __launch_bounds__(PTHREADS, 1)
   __shared__ int s_fail;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int nk = kext / BK;
+  const int nk = kext / (KIND == 0 ? BK : 2 * BK);  // stage = 128 bytes of K per row
 
   if (threadIdx.x == 0) {
     s_fail = 0;
@@ -226,8 +242,9 @@ __global__ void __launch_bounds__(PTHREADS, 1)
           if (*(volatile int*)&s_fail) break;
           unsigned char* sa = smem + s * STAGE_BYTES;
           mbar_expect_tx(&full[s], STAGE_BYTES);
-          tma_load_2d(sa, &tmA, kb * BK, ti * BM, &full[s]);
-          tma_load_2d(sa + TILE_BYTES, &tmB, kb * BK, tj * BN, &full[s]);
+          const int kx = kb * (KIND == 0 ? BK : 2 * BK);  // element coordinate of the stage
+          tma_load_2d(sa, &tmA, kx, ti * BM, &full[s]);
+          tma_load_2d(sa + TILE_BYTES, &tmB, kx, tj * BN, &full[s]);
           ++issued;
         }
         if (*(volatile int*)&s_fail) break;
@@ -257,9 +274,14 @@ __global__ void __launch_bounds__(PTHREADS, 1)
           const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
           const uint32_t sb = sa + TILE_BYTES;
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk)
-            tc_mma_f16(dacc, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
-                       (kb > 0 || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < 4; ++kk) {  // 4 x 32 bytes of K per stage
+            if (KIND == 0)
+              tc_mma_f16(dacc, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
+                         (kb > 0 || kk > 0) ? 1u : 0u);
+            else
+              tc_mma_f8(dacc, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
+                        (kb > 0 || kk > 0) ? 1u : 0u);
+          }
           tc_commit(&empty[s]);
         }
         tc_commit(&acc_full[a]);
@@ -285,6 +307,7 @@ __global__ void __launch_bounds__(PTHREADS, 1)
       }
       const int r = ti * BM + q * 32 + lane;
       const bool diag = (ti == tj);
+      const float scale = (KIND == 1) ? exp2f(-(float)((int)exps[ti] + (int)exps[tj])) : 1.0f;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t v[32];
@@ -303,7 +326,8 @@ __global__ void __launch_bounds__(PTHREADS, 1)
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int c = cb + j;
-            if (c < ncols && (!diag || r >= c)) cp[(size_t)c * ldc] = old[j] - __uint_as_float(v[j]);
+            if (c < ncols && (!diag || r >= c))
+              cp[(size_t)c * ldc] = old[j] - scale * __uint_as_float(v[j]);
           }
         }
       }
@@ -351,19 +375,41 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2D map over a row-major rows x cols matrix of 16-bit elements, box 64 x 128.
-static int make_map_16(CUtensorMap* map, const void* base, int rows, int cols, int ld,
-                       CUtensorMapDataType dt) {
+// 2D map over a row-major rows x cols matrix (element size esize bytes), box
+// of 128 bytes x 128 rows, 128-byte swizzle.
+static int make_map(CUtensorMap* map, const void* base, int rows, int cols, int ld, int esize,
+                    CUtensorMapDataType dt) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return JMG_ERR_CUDA;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BM};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * esize};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / esize), (cuuint32_t)tc::BM};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? JMG_OK : JMG_ERR_CUDA;
+}
+
+template <int KIND>
+static int syrk_persistent(int m, int ncols, int kext, const CUtensorMap& ma, const CUtensorMap& mb,
+                           int ab_fmt, const signed char* exps, float* C, int ldc, int* err,
+                           cudaStream_t s) {
+  static int attr_dev = -1, nsm = 0;
+  int dev = 0;
+  JMG_CUDA(cudaGetDevice(&dev));
+  if (attr_dev != dev) {
+    JMG_CUDA(cudaFuncSetAttribute(tc::k_syrk_tc<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tc::PSMEM_BYTES));
+    JMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    attr_dev = dev;
+  }
+  const int TI = cdiv(m, tc::BM), TJ = cdiv(ncols, tc::BN);
+  const long long ntiles = (long long)TJ * (TJ + 1) / 2 + (long long)(TI - TJ) * TJ;
+  const int grid = (int)std::min<long long>(ntiles, nsm);
+  tc::k_syrk_tc<KIND><<<grid, tc::PTHREADS, tc::PSMEM_BYTES, s>>>(
+      ma, mb, C, ldc, m, ncols, kext, ab_fmt, (int)ntiles, TJ, exps, err);
+  return launched();
 }
 
 int launch_syrk_tc(int m, int ncols, int kext, const void* PA, const void* PB, int ldp, int prec,
@@ -376,29 +422,22 @@ int launch_syrk_tc(int m, int ncols, int kext, const void* PA, const void* PB, i
   CUtensorMapDataType dt =
       prec == JMG_PREC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   CUtensorMap ma, mb;
-  JMG_TRY(make_map_16(&ma, PA, m, kext, ldp, dt));
-  JMG_TRY(make_map_16(&mb, PB, m, kext, ldp, dt));
-  static int attr_dev = -1;
-  int dev = 0;
-  JMG_CUDA(cudaGetDevice(&dev));
-  static int nsm = 0;
-  if (attr_dev != dev) {
-    JMG_CUDA(cudaFuncSetAttribute(tc::k_syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  tc::PSMEM_BYTES));
-    JMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    attr_dev = dev;
-  }
-  const int TI = cdiv(m, tc::BM), TJ = cdiv(ncols, tc::BN);
-  const long long ntiles = (long long)TJ * (TJ + 1) / 2 + (long long)(TI - TJ) * TJ;
-  const int grid = (int)std::min<long long>(ntiles, nsm);
-  tc::k_syrk_tc<<<grid, tc::PTHREADS, tc::PSMEM_BYTES, s>>>(
-      ma, mb, C, ldc, m, ncols, kext, prec == JMG_PREC_BF16 ? 1 : 0, (int)ntiles, TJ, err);
-  return launched();
+  JMG_TRY(make_map(&ma, PA, m, kext, ldp, 2, dt));
+  JMG_TRY(make_map(&mb, PB, m, kext, ldp, 2, dt));
+  return syrk_persistent<0>(m, ncols, kext, ma, mb, prec == JMG_PREC_BF16 ? 1 : 0, nullptr, C, ldc,
+                            err, s);
 }
 
-int launch_syrk_fp8(int, int, const void*, int, const signed char*, float*, int, int*,
-                    cudaStream_t) {
-  return JMG_ERR_UNSUPPORTED;
+int launch_syrk_fp8(int m, int ncols, int kext, const void* Q, int ldq, const signed char* e,
+                    float* C, int ldc, int* err, cudaStream_t s) {
+  if (m <= 0 || ncols <= 0 || kext <= 0) return JMG_OK;
+  if (ncols > m) return JMG_ERR_UNSUPPORTED;
+  if (kext % 128 || ldq % 128 || ldq < kext) return JMG_ERR_ALIGN;
+  if (reinterpret_cast<uintptr_t>(Q) & 15) return JMG_ERR_ALIGN;
+  if (!e) return JMG_ERR_UNSUPPORTED;
+  CUtensorMap mq;
+  JMG_TRY(make_map(&mq, Q, m, kext, ldq, 1, CU_TENSOR_MAP_DATA_TYPE_UINT8));
+  return syrk_persistent<1>(m, ncols, kext, mq, mq, 0, e, C, ldc, err, s);
 }
 
 }  // namespace jmg

@@ -121,7 +121,13 @@ int launch_sym_grad(int n, int nrhs, const double* Bb, int ldb, const double* X,
 // row-major 16-bit words; ncols <= m.
 int launch_syrk_tc(int m, int ncols, int kext, const void* PA, const void* PB, int ldp, int prec,
                    float* C, int ldc, int* err, cudaStream_t s);
-int launch_syrk_fp8(int m, int kext, const void* Q, int ldq, const signed char* e, float* C,
-                    int ldc, int* err, cudaStream_t s);
+// FP8 e4m3 variant: Q (m x kext bytes, row-major, ldq), C -= 2^-(e[ti]+e[tj]) Q_ti Q_tj^T
+int launch_syrk_fp8(int m, int ncols, int kext, const void* Q, int ldq, const signed char* e,
+                    float* C, int ldc, int* err, cudaStream_t s);
+// Quantise the FP32 panel L21 (m x kb, ldw) to e4m3 with one power-of-two scale
+// per 128-row tile: e = floor(log2(448 / amax)) clamped to [-126, 126] (0 for an
+// all-zero tile), Q = rn_satfinite(x * 2^e), row-major m x kb (ldq bytes).
+int launch_quant_fp8(int m, int kb, const float* L21, int ldw, void* Q, int ldq, signed char* e,
+                     cudaStream_t s);
 
 }  // namespace jmg

@@ -79,7 +79,7 @@ _SIGS = {
     "jmg_status_string": (ctypes.c_char_p, [_I]),
     "jmg_sym_grad": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P]),
     "jmg_dev_syrk_tc": (_I, [_I, _I, _I, _P, _P, _I, _I, _P, _I, _P, _P]),
-    "jmg_dev_syrk_fp8": (_I, [_I, _I, _P, _I, _P, _P, _I, _P, _P]),
+    "jmg_dev_syrk_fp8": (_I, [_I, _I, _I, _P, _I, _P, _P, _I, _P, _P]),
     "jmg_dev_residual_workspace": (_SZ, [_I, _I]),
     "jmg_dev_residual": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P, _SZ, _P]),
     "jmg_dev_norm_inf": (_I, [_I, _P, _I, _P, _P, _SZ, _P]),
@@ -341,6 +341,24 @@ def syrk_tc_(C: torch.Tensor, PA: torch.Tensor, PB: torch.Tensor | None = None,
                                 PB.data_ptr(), kext, prec, pc, ldc, err.data_ptr(),
                                 _stream(C.device))
     _chk(st, "jmg_dev_syrk_tc")
+    return err
+
+
+def syrk_fp8_(C: torch.Tensor, Q: torch.Tensor, e: torch.Tensor,
+              ncols: int | None = None) -> torch.Tensor:
+    """C_lower -= 2^-(e_i + e_j) Q_i Q_j^T (e4m3 Q: m x kext row-major bytes, e: int8
+    exponent per 128-row tile; C: FP32 column-major)."""
+    _need_cuda(C, Q, e)
+    if Q.dtype not in (torch.uint8, getattr(torch, "float8_e4m3fn", torch.uint8)) or not Q.is_contiguous():
+        raise TypeError("syrk_fp8_: Q must be contiguous e4m3 bytes")
+    if e.dtype != torch.int8:
+        raise TypeError("syrk_fp8_: e must be int8")
+    m, kext = Q.shape
+    pc, ldc = _colmajor(C, "C")
+    err = torch.zeros(1, dtype=torch.int32, device=C.device)
+    st = load().jmg_dev_syrk_fp8(m, m if ncols is None else ncols, kext, Q.data_ptr(), kext,
+                                 e.data_ptr(), pc, ldc, err.data_ptr(), _stream(C.device))
+    _chk(st, "jmg_dev_syrk_fp8")
     return err
 
 

@@ -92,6 +92,20 @@ def test_posv_mixed_high_kappa(kappa, prec, words, refine):
     _check(A, B, X, kappa)
 
 
+@pytest.mark.parametrize("n,nrhs,shift", [(700, 4, 1e-2), (2000, 8, 1e-2), (1500, 2, 1.0)])
+def test_posv_fp8_tile_scaled(n, nrhs, shift):
+    # e4m3 trailing updates with one power-of-two scale per 128 x 128 panel
+    # tile, FP64 refinement (PCG and the diagonal shift as needed) to 1e-13
+    A = inputs.gram_shift(n, shift, seed=inputs.seed_for("fp8", n))
+    Xt = inputs.uniform(n, nrhs, seed=8)
+    B = inputs.rhs_from(A, Xt)
+    Ad, _ = to_dev_colmajor(lower_only(A))
+    Bd, _ = to_dev_colmajor(B)
+    X, si = jmg.posv(Ad, Bd, prec="fp8", maxit=300)
+    assert si.status == 0, si
+    _check(A, B, X, kappa=1e3)
+
+
 def test_posv_reuse_factor():
     # a refine-only call with the factor left in the workspace by a first call
     n, nrhs = 700, 3

@@ -187,3 +187,29 @@ def test_syrk_tc_exact_integers(m, ncols, kext, dtype):
     touched[:, ncols:] = False
     assert np.array_equal(got[touched], w[touched])
     assert np.array_equal(got[~touched], C0.numpy()[~touched]), "outside the trapezoid was written"
+
+
+@pytest.mark.parametrize("m,ncols,kext", [(1, 1, 128), (300, 300, 128), (2600, 2600, 128),
+                                          (2600, 900, 256)])
+def test_syrk_fp8_exact_integers(m, ncols, kext):
+    # e4m3 holds the integers -8..8 exactly; products <= 64, sums over kext and
+    # power-of-two tile scales stay exact in FP32: the update must be bit-exact
+    g = torch.Generator().manual_seed(m + kext)
+    Qv = torch.randint(-8, 9, (m, kext), generator=g).to(torch.float64)
+    ntile = (m + 127) // 128
+    e = torch.randint(-3, 4, (ntile,), generator=g, dtype=torch.int8)
+    C0 = torch.randint(-1000, 1000, (m, m), generator=g).to(torch.float64)
+    sc = torch.pow(2.0, -e.to(torch.float64))
+    rs = sc.repeat_interleave(128)[:m]
+    want = C0 - (rs[:, None] * Qv) @ (rs[:, None] * Qv).t()
+    Q8 = Qv.to(torch.float32).to(torch.float8_e4m3fn).view(torch.uint8).contiguous().to(DEV)
+    Cd, _ = to_dev_colmajor(C0)
+    Cf = Cd.to(torch.float32).t().contiguous().t()
+    err = jmg.syrk_fp8_(Cf, Q8, e.to(DEV), ncols=ncols)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    got = Cf.double().cpu().numpy()
+    touched = np.tril(np.ones((m, m), dtype=bool))
+    touched[:, ncols:] = False
+    assert np.array_equal(got[touched], want.numpy()[touched])
+    assert np.array_equal(got[~touched], C0.numpy()[~touched])
