@@ -128,6 +128,30 @@ int jmg_potrs(int n, int nrhs, const void* L, int lda, void* B, int ldb, int dty
               void* work, size_t lwork, void* stream);
 
 /*
+ * potrs_static -- jmg_potrs without a `work` buffer.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate device
+ * memory when they solve -- code running under a fixed device-memory budget
+ * handed out at start-up, a host framework that owns every device byte through
+ * its own pool, or plain C callers without a device allocator -- and so cannot
+ * pass the scratch that jmg_potrs wants.  It allocates nothing (no cudaMalloc,
+ * no cudaFree, no allocating library routine); its scratch is a fixed 64 KiB
+ * array in device memory that every GPU loading the library keeps until the
+ * process exits.
+ *   Arguments and results as jmg_potrs (FP64 only).
+ *   Limit: ceil(nrhs/16) * (1 + ceil(n/128)) + 1 <= 16384 ints of scratch
+ *     (e.g. nrhs <= 496 at n = 65536); larger problems return JMG_ERR_WORKSPACE
+ *     with nothing queued.
+ *   The first call on a device, with that device current, looks up the device
+ *     address of the array (cudaGetSymbolAddress); make that first call before
+ *     any stream capture.
+ *   Every call shares the one array, which keeps the last call's contents (the
+ *     call clears what must start at zero): calls that overlap on the GPU (for
+ *     example on two streams) race and must not be issued.
+ */
+int jmg_potrs_static(int n, int nrhs, const void* L, int lda, void* B, int ldb, int dtype,
+                     void* stream);
+
+/*
  * posv -- solve A X = B (paper: "Software design", potrs as one call).
  *   prec == NATIVE: potrf then potrs, in place (A becomes L), asynchronous.
  *   prec != NATIVE: A is PRESERVED (it is needed for the FP64 residual).  The

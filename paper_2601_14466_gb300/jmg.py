@@ -73,6 +73,7 @@ _SIGS = {
     "jmg_workspace_size": (_SZ, [_I, _I, _I, _I, ctypes.POINTER(Options)]),
     "jmg_potrf": (_I, [_I, _P, _I, _I, _P, ctypes.POINTER(Options), _P, _SZ, _P]),
     "jmg_potrs": (_I, [_I, _I, _P, _I, _P, _I, _I, _P, _SZ, _P]),
+    "jmg_potrs_static": (_I, [_I, _I, _P, _I, _P, _I, _I, _P]),
     "jmg_posv": (_I, [_I, _I, _P, _I, _P, _I, _I, _P, ctypes.POINTER(Options),
                       ctypes.POINTER(Stats), _P, _SZ, _P]),
     "jmg_logdet": (_I, [_I, _P, _I, _I, _P, _P]),
