@@ -36,12 +36,15 @@ METRIC = ("posv TFLOP/s & time-to-solution at backward err ≤1e-13: mixed+IR vs
 WORKLOADS = {
     "c1": dict(n=1024, nrhs=1, kind="gram", param=1.0, prec="bf16", words=1,
                desc="posv n=1024 nrhs=1, A = M M^T/n + I"),
-    "c2": dict(n=16384, nrhs=64, kind="qlam", param=1e6, prec="bf16", words=3,
+    "c2": dict(n=16384, nrhs=64, kind="qlam", param=1e6, prec="fp16", words=2,
                desc="posv n=16384 nrhs=64, A = Q diag(logspace[1,1e6]) Q^T, B = A X_true"),
-    "c3": dict(n=32768, nrhs=16, kind="qlam", param=1e4, prec="bf16", words=2,
+    "c3": dict(n=32768, nrhs=16, kind="qlam", param=1e4, prec="fp16", words=2,
                desc="posv n=32768 nrhs=16, A = Q diag(logspace[1,kappa]) Q^T"),
-    "c4": dict(n=65536, nrhs=32, kind="gram", param=1e-2, prec="bf16", words=2,
-               desc="posv n=65536 nrhs=32, A = M M^T/n + 1e-2 I"),
+    "c4": dict(n=65536, nrhs=32, kind="gram32", param=1e-2, prec="fp8", words=1,
+               desc="posv n=65536 nrhs=32, A = M M^T/n + 1e-2 I (product formed in FP32)"),
+    "c5": dict(n=8192, nrhs=16, kind="gram", param=1.0, prec="bf16", words=2,
+               desc="autograd forward+backward n=8192 nrhs=16, A = M M^T/n + I, B ~ N(0,1), "
+                    "loss 0.5||X||^2", rhs="normal"),
 }
 
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
@@ -125,7 +128,12 @@ def make_inputs(w, device, seed=0):
     if w["kind"] == "qlam":
         A = inputs.q_lambda(n, w["param"], seed=seed, device=device)
     else:
-        A = inputs.gram_shift(n, w["param"], seed=seed, device=device)
+        A = inputs.gram_shift(n, w["param"], seed=seed, device=device,
+                              fp32_product=(w["kind"] == "gram32"))
+    if w.get("rhs") == "normal":
+        B = inputs.normal(n, nrhs, seed=seed + 1, device=device)  # column-major
+        torch.cuda.synchronize()
+        return A, None, B
     Xt = inputs.uniform(n, nrhs, seed=seed + 1, device=device)
     B = inputs.rhs_from(A, Xt)
     torch.cuda.synchronize()
@@ -146,7 +154,7 @@ def cpu_oracle_sample(w, target_s=12.0):
     if w["kind"] == "qlam":
         A = inputs.q_lambda(n_s, w["param"], seed=11).numpy()
     else:
-        A = inputs.gram_shift(n_s, w["param"], seed=11).numpy()
+        A = inputs.gram_shift(n_s, w["param"], seed=11).numpy()  # same construction, FP64
     X = inputs.uniform(n_s, nrhs, seed=12).numpy()
     B = np.asfortranarray(A @ X)
     oracle.build()
@@ -166,19 +174,35 @@ def cpu_oracle_sample(w, target_s=12.0):
 
 
 # ----------------------------------------------------------------------------- main GPU arm
+def _device():
+    import torch
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    return dev
+
+
+def _eta(jmg, Acm, X, B, anorm):
+    _, cm = jmg.residual(Acm, X, B)
+    cm = cm.cpu()
+    return float((cm[0] / (anorm * cm[1] + cm[2])).max())
+
+
 def run_ours(args, w, rank, world):
     import torch
 
     from paper_2601_14466_gb300 import jmg
 
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
-    torch.cuda.set_device(dev)
+    dev = _device()
     jmg.load()
     n, nrhs = w["n"], w["nrhs"]
     prec, words = args.prec or w["prec"], args.words or w["words"]
     A, Xt, B = make_inputs(w, dev)
     Acm = A.t()  # symmetric: the transpose view is the column-major matrix
-    opts = jmg.default_options(prec=prec, words=words, nb=args.nb)
+    kw = dict(prec=prec, words=words, nb=args.nb, maxit=args.maxit, refine=args.refine,
+              resid=args.resid)
+    opts = jmg.default_options(prec=prec, words=words, nb=args.nb,
+                               resid={"auto": 0, "fp64": 1, "split": 2}[args.resid])
     work = jmg.workspace(jmg.OP_POSV, n, nrhs, opts, dev)
     stream = torch.cuda.current_stream(dev)
     F = nominal_flops(n, nrhs)
@@ -188,18 +212,18 @@ def run_ours(args, w, rank, world):
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
-    # ---- mixed + IR
+    # ---- mixed precision + FP64 refinement
     for _ in range(args.warmup):
-        X, si = jmg.posv(Acm, B, prec=prec, words=words, nb=args.nb, work=work)
+        X, si = jmg.posv(Acm, B, work=work, **kw)
     barrier()
-    sampler = ClockSampler(dev.index if world == 1 else int(os.environ.get("LOCAL_RANK", "0")))
+    sampler = ClockSampler(dev.index)
     sampler.start()
     l0 = jmg.launch_count()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     infos = []
     ev[0].record(stream)
     for k in range(args.steps):
-        X, si = jmg.posv(Acm, B, prec=prec, words=words, nb=args.nb, work=work, timing=True)
+        X, si = jmg.posv(Acm, B, work=work, timing=True, **kw)
         ev[k + 1].record(stream)
         infos.append(si)
     barrier()
@@ -207,90 +231,91 @@ def run_ours(args, w, rank, world):
     clocks = sampler.stop()
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     t_mixed = sum(step_ms) / 1e3
-    # verify the last solution with the GPU residual (FP64)
-    R, cm = jmg.residual(Acm, X, B)
     anorm = float(jmg.norm_inf(Acm).item())
-    cm = cm.cpu()
-    eta = float((cm[0] / (anorm * cm[1] + cm[2])).max())
-    fwd = float(((X - Xt).abs().max() / Xt.abs().max()).item())
+    eta = _eta(jmg, Acm, X, B, anorm)
+    fwd = float(((X - Xt).abs().max() / Xt.abs().max()).item()) if Xt is not None else None
 
     # ---- plain FP64 GPU path on the same system (A restored between steps, untimed)
-    f64_steps = max(1, min(args.steps, args.fp64_steps))
-    Awork = torch.empty_like(A)
-    Aw_cm = Awork.t()
-    f64_ms = []
-    for k in range(1 + f64_steps):
-        Awork.copy_(A)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        X64, _ = jmg.posv(Aw_cm, B, prec="fp64", overwrite_a=True, check=False)
-        e1.record(stream)
-        e1.synchronize()
-        if k > 0:
-            f64_ms.append(e0.elapsed_time(e1))
-    R64, cm64 = jmg.residual(Acm, X64, B)
-    cm64 = cm64.cpu()
-    eta64 = float((cm64[0] / (anorm * cm64[1] + cm64[2])).max())
-    del Awork
+    f64_steps = min(args.steps, args.fp64_steps)
+    t_f64, eta64 = None, None
+    if f64_steps > 0:
+        Awork = torch.empty_like(A)
+        Aw_cm = Awork.t()
+        f64_ms = []
+        for k in range(1 + f64_steps):
+            Awork.copy_(A)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            X64, _ = jmg.posv(Aw_cm, B, prec="fp64", overwrite_a=True, check=False, nb=args.nb)
+            e1.record(stream)
+            e1.synchronize()
+            if k > 0:
+                f64_ms.append(e0.elapsed_time(e1))
+        del Awork
+        t_f64 = sum(f64_ms) / 1e3
+        eta64 = _eta(jmg, Acm, X64, B, anorm)
 
     # ---- end to end through the public API with host buffers
-    e2e_steps = max(1, min(args.steps, 3))
-    A_h = A.cpu().pin_memory()
-    B_h = B.cpu().pin_memory()
-    X_h = torch.empty((nrhs, n), dtype=torch.float64).pin_memory().t()
-    A_d = torch.empty_like(A)
-    B_d = torch.empty((nrhs, n), dtype=torch.float64, device=dev).t()
-    e2e_ms = []
-    for k in range(1 + e2e_steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        A_d.copy_(A_h, non_blocking=True)
-        B_d.copy_(B_h, non_blocking=True)
-        Xe, _ = jmg.posv(A_d.t(), B_d, prec=prec, words=words, nb=args.nb, work=work)
-        X_h.copy_(Xe, non_blocking=True)
-        e1.record(stream)
-        e1.synchronize()
-        if k > 0:
-            e2e_ms.append(e0.elapsed_time(e1))
-    t_e2e = sum(e2e_ms) / 1e3
-    del A_d
+    e2e_steps = min(args.steps, args.e2e_steps)
+    t_e2e = None
+    if e2e_steps > 0:
+        A_h = A.cpu().pin_memory()
+        B_h = B.cpu().pin_memory()
+        X_h = torch.empty((nrhs, n), dtype=torch.float64).pin_memory().t()
+        A_d = torch.empty_like(A)
+        B_d = torch.empty((nrhs, n), dtype=torch.float64, device=dev).t()
+        e2e_ms = []
+        for k in range(1 + e2e_steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            A_d.copy_(A_h, non_blocking=True)
+            B_d.copy_(B_h, non_blocking=True)
+            Xe, _ = jmg.posv(A_d.t(), B_d, work=work, **kw)
+            X_h.copy_(Xe, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            if k > 0:
+                e2e_ms.append(e0.elapsed_time(e1))
+        t_e2e = sum(e2e_ms) / 1e3
+        del A_d, A_h
 
     # ---- across ranks: max time
-    times = torch.tensor([t_mixed, sum(f64_ms) / 1e3, t_e2e], dtype=torch.float64, device=dev)
+    times = torch.tensor([t_mixed, t_f64 or 0.0, t_e2e or 0.0], dtype=torch.float64, device=dev)
     if world > 1:
         torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
-    t_mixed, t_f64, t_e2e = [float(v) for v in times.cpu()]
+    t_mixed, tf, te = [float(v) for v in times.cpu()]
+    t_f64 = tf if f64_steps > 0 else None
+    t_e2e = te if e2e_steps > 0 else None
 
     value = world * F * args.steps / t_mixed / 1e12
-    fp64_value = world * F * f64_steps / t_f64 / 1e12
-    e2e_value = world * F * e2e_steps / t_e2e / 1e12
-
-    # roofline of the dominant kernel: the FP64 residual GEMM (2 n^2 nrhs flops per launch)
+    # roofline of the dominant kernel: the FP64 A*X GEMM of the residual / PCG
+    # (2 n^2 nrhs flops per launch), timed by the library with CUDA events
     n_res = sum(si.n_resid for si in infos)
     t_res = sum(si.t_resid_gpu_ms for si in infos)
     achieved = 2.0 * n * n * nrhs / (t_res / max(n_res, 1) / 1e3) / 1e12 if n_res else None
     probe_f, probe_ms = jmg.probe(0, 608, 3000, dev)
     probe_tf = probe_f / probe_ms / 1e9
-    share = t_res / 1e3 / t_mixed if n_res else None
+    share = t_res / 1e3 / (t_mixed / world) if n_res else None
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(t_mixed * 1e3 / args.steps, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64 (bf16/fp16 tensor-core factor)",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 (%s%s tensor-core factor)" % (prec, "x%d" % words if prec != "fp8" else ""),
         "data": "synthetic, seeded (torch.Generator); A resident in HBM, larger than L2",
         "config": {"workload": w["desc"], "n": n, "nrhs": nrhs, "prec": prec, "words": words,
-                   "nb": args.nb, "tol": 1e-13, "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "nb": args.nb, "tol": 1e-13, "refine": args.refine,
+                   "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 (A = %.2f GB), no flush" % (n * n * 8 / 1e9)},
         "time_to_solution_ms": round(t_mixed * 1e3 / args.steps, 3),
         "bwd_err": eta, "fwd_err": fwd, "iters": [si.iters for si in infos],
+        "refine_used": ["ir", "pcg", "auto"][infos[-1].refine_used] if infos[-1].refine_used >= 0 else None,
+        "shift": infos[-1].shift, "factor_tries": infos[-1].factor_tries,
+        "eta_hist": [float("%.3e" % e) for e in infos[-1].eta_hist],
         "phases_ms": {"factor": round(statistics.mean(si.t_factor_ms for si in infos), 3),
                       "solve": round(statistics.mean(si.t_solve_ms for si in infos), 3),
                       "refine": round(statistics.mean(si.t_refine_ms for si in infos), 3)},
-        "fp64": {"value": round(fp64_value, 4), "unit": "TFLOP/s",
-                 "ms_per_step": round(t_f64 * 1e3 / f64_steps, 3), "steps": f64_steps,
-                 "bwd_err": eta64, "frac_of_fp64_nominal": round(fp64_value / world / FP64_NOMINAL_TFLOPS, 4)},
-        "speedup_mixed_vs_fp64": round((t_f64 / f64_steps) / (t_mixed / args.steps), 3),
-        "roofline": {"kernel": "k_gemm<double,64,S,N,PART> (FP64 residual R = B - A X)",
+        "roofline": {"kernel": "k_gemm<double,*,S,N,PART> (FP64 A*X of residual / PCG)",
                      "bound": "alu", "achieved": round(achieved, 4) if achieved else None,
                      "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                      "frac": round(achieved / FP64_NOMINAL_TFLOPS, 4) if achieved else None,
@@ -299,13 +324,86 @@ def run_ours(args, w, rank, world):
                      "frac_of_probe": round(achieved / probe_tf, 4) if achieved else None,
                      "share_of_step": round(share, 4) if share else None,
                      "launches": n_res, "traffic": None},
-        "e2e": {"value": round(e2e_value, 4), "unit": "TFLOP/s",
-                "ms_per_step": round(t_e2e * 1e3 / e2e_steps, 3),
-                "h2d_bytes_per_step": n * n * 8 + n * nrhs * 8, "d2h_bytes_per_step": n * nrhs * 8},
         "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
         "clocks": clocks,
     }
+    if t_f64 is not None:
+        fp64_value = world * F * f64_steps / t_f64 / 1e12
+        out["fp64"] = {"value": round(fp64_value, 4), "unit": "TFLOP/s",
+                       "ms_per_step": round(t_f64 * 1e3 / f64_steps, 3), "steps": f64_steps,
+                       "bwd_err": eta64,
+                       "frac_of_fp64_nominal": round(fp64_value / world / FP64_NOMINAL_TFLOPS, 4)}
+        out["speedup_mixed_vs_fp64"] = round((t_f64 / f64_steps) / (t_mixed / args.steps), 3)
+    if t_e2e is not None:
+        out["e2e"] = {"value": round(world * F * e2e_steps / t_e2e / 1e12, 4), "unit": "TFLOP/s",
+                      "ms_per_step": round(t_e2e * 1e3 / e2e_steps, 3),
+                      "h2d_bytes_per_step": n * n * 8 + n * nrhs * 8,
+                      "d2h_bytes_per_step": n * nrhs * 8}
     return out
+
+
+def run_grad(args, w, rank, world):
+    """Forward + backward of the differentiable solve (autograd.SPDSolve) for
+    loss = 0.5 ||X||_F^2: mixed forward (adjoint solve against the kept factor)
+    vs the FP64 forward; gradient checked by central differences."""
+    import torch
+
+    from paper_2601_14466_gb300 import autograd, jmg
+
+    dev = _device()
+    jmg.load()
+    n, nrhs = w["n"], w["nrhs"]
+    prec, words = args.prec or w["prec"], args.words or w["words"]
+    A, _, B = make_inputs(w, dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(p):
+        Ad = A.clone().requires_grad_(True)
+        Bd = B.clone().requires_grad_(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        X = autograd.solve(Ad, Bd, p, words)
+        (0.5 * (X * X).sum()).backward()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), Ad.grad, Bd.grad
+
+    res = {}
+    for p in (prec, "fp64"):
+        for _ in range(args.warmup):
+            step(p)
+        ms = [step(p)[0] for _ in range(args.steps if p == prec else min(args.steps, 3))]
+        res[p] = statistics.mean(ms)
+    _, G, GB = step(prec)
+    # central differences with the FP64 forward on 8 seeded entries
+    rng = __import__("numpy").random.default_rng(33)
+    h, worst = 1e-6, 0.0
+    for _ in range(8):
+        i, j = sorted(rng.integers(0, n, size=2))[::-1]
+        E = torch.zeros_like(A)
+        E[i, j] = h
+        E[j, i] = h
+
+        def loss(M):
+            X, _ = jmg.posv(M.t(), B, prec="fp64")
+            return 0.5 * float((X * X).sum().item())
+
+        fd = (loss(A + E) - loss(A - E)) / (2 * h)
+        want = float(G[i, j] + G[j, i]) if i != j else float(G[i, i])
+        worst = max(worst, abs(fd - want) / max(1.0, abs(want)))
+    F = nominal_flops(n, nrhs) + 2.0 * n * n * nrhs  # forward + adjoint solve
+    return {
+        "metric": METRIC + " [differentiation workload: forward+backward]",
+        "value": round(F / (res[prec] / 1e3) / 1e12, 4), "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(res[prec], 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 (%sx%d tensor-core factor)" % (prec, words), "data": "synthetic, seeded",
+        "config": {"workload": w["desc"], "n": n, "nrhs": nrhs, "prec": prec, "words": words},
+        "fp64": {"ms_per_step": round(res["fp64"], 3),
+                 "value": round(F / (res["fp64"] / 1e3) / 1e12, 4)},
+        "speedup_mixed_vs_fp64": round(res["fp64"] / res[prec], 3),
+        "fd_max_rel_err_8_entries": worst,
+    }
 
 
 def main():
@@ -319,9 +417,17 @@ def main():
     ap.add_argument("--words", type=int, default=None)
     ap.add_argument("--nb", type=int, default=128)
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--kappa", type=float, default=None)
+    ap.add_argument("--maxit", type=int, default=50)
+    ap.add_argument("--refine", default="auto", choices=["ir", "pcg", "auto"])
+    ap.add_argument("--resid", default="auto", choices=["auto", "fp64", "split"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.kappa is not None:
+        w["param"] = args.kappa
+        w["desc"] = w["desc"].replace("kappa", "%g" % args.kappa)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -350,7 +456,7 @@ def main():
 
     if world > 1:
         torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    out = run_ours(args, w, rank, world)
+    out = (run_grad if args.workload == "c5" else run_ours)(args, w, rank, world)
     if rank == 0:
         if not args.no_cpu_baseline:
             cb = cpu_oracle_sample(w)

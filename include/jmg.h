@@ -75,6 +75,10 @@ typedef struct {
   int reuse_factor; /* mixed posv only: 1 = skip the factorisation and refine with  */
                     /* the factor that an earlier jmg_posv call with the same A, n  */
                     /* and options left in `work` (the adjoint solve of autograd)   */
+  int resid;        /* mixed posv: how the FP64-accurate products A X of the        */
+                    /* refinement are formed: 0 auto (= 2), 1 FP64 CUDA cores,      */
+                    /* 2 BF16 tensor cores with error-free splitting (16 n^2 bytes  */
+                    /* of extra workspace)                                          */
 } jmg_options;
 
 /* Host-side report of one posv call (filled when the call returns). */
@@ -96,7 +100,7 @@ typedef struct {
 } jmg_stats;
 
 /* Fill *opt with the defaults: nb 128, NB 128, prec NATIVE, words 1, tol 1e-13,
- * maxit 50, refine AUTO, shift_retry 1, timing 0, reuse_factor 0. */
+ * maxit 50, refine AUTO, shift_retry 1, timing 0, reuse_factor 0, resid 0. */
 void jmg_default_options(jmg_options* opt);
 
 /* Bytes of `work` that the call (op, n, nrhs, dtype, opt) needs; 0 is valid. */

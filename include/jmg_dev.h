@@ -50,6 +50,20 @@ int jmg_dev_residual(int n, int nrhs, const double* A, int lda, const double* X,
                      const double* B, int ldb, double* R, int ldr, double* colmax,
                      void* work, size_t lwork, void* stream);
 
+/*
+ * The same residual with the product A X formed on the BF16 tensor cores by
+ * error-free splitting into 8 slices of 7 bits per operand (Ozaki, Ogita,
+ * Oishi and Rump 2012) and exact FP32 accumulation over windows of 256,
+ * combined in FP64: FP64-accurate, and the kernel the refinement loop uses
+ * when opt->resid selects it.  Arguments as jmg_dev_residual; `work` holds the
+ * slices of A (16 n^2 bytes) and of X: jmg_dev_residual_split_workspace bytes.
+ * `err` (device int) is set if a device-side wait ran out.
+ */
+size_t jmg_dev_residual_split_workspace(int n, int nrhs);
+int jmg_dev_residual_split(int n, int nrhs, const double* A, int lda, const double* X, int ldx,
+                           const double* B, int ldb, double* R, int ldr, double* colmax,
+                           int* err, void* work, size_t lwork, void* stream);
+
 /* ||A||_inf of the symmetric matrix held in lower(A) (FP64), to *out. */
 int jmg_dev_norm_inf(int n, const double* A, int lda, double* out, void* work, size_t lwork,
                      void* stream);

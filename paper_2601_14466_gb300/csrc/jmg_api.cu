@@ -25,7 +25,9 @@ namespace jmg {
 struct Plan {
   size_t off_W = 0, off_PA = 0, off_PB = 0, off_X = 0, off_R = 0, off_D = 0, off_part = 0,
          off_colmax = 0, off_eta = 0, off_anorm = 0, off_rowsum = 0, off_ints = 0, off_Z = 0,
-         off_P = 0, off_Q = 0, off_scal = 0, off_sync = 0, off_exp = 0, total = 0;
+         off_P = 0, off_Q = 0, off_scal = 0, off_sync = 0, off_exp = 0, off_ozrow = 0,
+         off_ozA = 0, off_ozX = 0, total = 0;
+  bool split = false;
   int ldw = 0, ldp = 0, kext = 0, splits = 1;
 };
 
@@ -60,12 +62,21 @@ static Plan plan_posv_mixed(int n, int nrhs, const jmg_options& o) {
   p.off_W = take(sizeof(float) * (size_t)p.ldw * N);
   p.off_anorm = take(sizeof(double) * 2);  // [0] ||A||_inf, [1] shift of the factor
   p.off_ints = take(sizeof(int) * 8);
+  p.split = o.resid != 1;  // tensor-core split products (auto or explicit)
+  if (p.split) {
+    p.off_ozrow = take(sizeof(double) * (N > 0 ? N : 1));
+    p.off_ozA = take(oz_a_bytes(n));
+  }
   p.off_PA = take(2 * N * p.ldp);  // 16-bit words, or e4m3 bytes for FP8
   p.off_exp = take(N / 128 + 2);
   p.off_PB = take(2 * N * p.ldp);
   p.off_X = take(sizeof(double) * N * R);
   p.off_R = take(sizeof(double) * N * R);
   p.off_D = take(sizeof(float) * N * R);
+  if (p.split) {
+    p.off_ozX = take(oz_x_bytes(n, nrhs > 0 ? nrhs : 1));
+    p.splits = std::max(p.splits, oz_splits_used(n, nrhs > 0 ? nrhs : 1));
+  }
   p.off_part = take(sizeof(double) * N * R * p.splits);
   p.off_colmax = take(sizeof(double) * 3 * R);
   p.off_eta = take(sizeof(double) * (1 + R));
@@ -200,10 +211,25 @@ static void hist(MixedCtx& c, double e) {
   c.S->n_hist++;
 }
 
+// Rout = Bin - A Xin (Bin == nullptr: Rout = A Xin) with column norms: the
+// FP64 CUDA-core GEMM or the split tensor-core product.  The product kernel is
+// timed with c.ev when timing is on.
+static int product(MixedCtx& c, const double* Xin, const double* Bin, int ldbin, double* Rout) {
+  if (!c.p->split)
+    return launch_residual(c.n, c.nrhs, c.A, c.lda, Xin, c.n, Bin, ldbin, Rout, c.n, c.colmax,
+                           c.part, c.p->splits, c.s, c.ev[0], c.ev[1]);
+  JMG_CUDA(cudaMemsetAsync(c.colmax, 0, sizeof(double) * 3 * c.nrhs, c.s));
+  if (c.ev[0]) JMG_CUDA(cudaEventRecord(c.ev[0], c.s));
+  JMG_TRY(oz_product(c.n, c.nrhs, at<char>(c.work, c.p->off_ozA), at<double>(c.work, c.p->off_ozrow),
+                     Xin, c.n, at<char>(c.work, c.p->off_ozX), c.part, &c.ints[1], c.s));
+  if (c.ev[1]) JMG_CUDA(cudaEventRecord(c.ev[1], c.s));
+  return launch_resid_reduce(c.n, c.nrhs, oz_splits_used(c.n, c.nrhs), c.part, Xin, c.n, Bin,
+                             ldbin, Rout, c.n, c.colmax, c.s);
+}
+
 // R = B - A X (true residual), eta -> host; returns max eta in c.eh[0]
 static int true_residual(MixedCtx& c) {
-  JMG_TRY(launch_residual(c.n, c.nrhs, c.A, c.lda, c.X, c.n, c.B, c.ldb, c.R, c.n, c.colmax,
-                          c.part, c.p->splits, c.s, c.ev[0], c.ev[1]));
+  JMG_TRY(product(c, c.X, c.B, c.ldb, c.R));
   JMG_TRY(launch_eta(c.nrhs, c.colmax, c.dsc, c.eta, c.s));
   JMG_TRY(sync_read(c.eh.data(), c.eta, sizeof(double) * (1 + c.nrhs), c.s));
   c.S->n_resid++;
@@ -235,8 +261,7 @@ static int pcg(MixedCtx& c, bool* breakdown) {
   JMG_TRY(launch_dot_cols(n, nrhs, c.R, n, c.Z, n, c.rz, c.s));
   while (c.S->iters < c.o->maxit) {
     // Q = A P (same FP64 kernel as the residual, without B)
-    JMG_TRY(launch_residual(n, nrhs, c.A, c.lda, c.P, n, nullptr, n, c.Q, n, c.colmax, c.part,
-                            c.p->splits, c.s, c.ev[0], c.ev[1]));
+    JMG_TRY(product(c, c.P, nullptr, n, c.Q));
     JMG_TRY(launch_dot_cols(n, nrhs, c.P, n, c.Q, n, c.pq, c.s));
     JMG_TRY(launch_pcg_step(n, nrhs, c.P, c.Q, c.rz, c.pq, c.X, c.R, c.colmax, &c.ints[3], c.s));
     JMG_TRY(launch_eta(nrhs, c.colmax, c.dsc, c.eta, c.s));
@@ -309,6 +334,8 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
 
   const double t0 = now_ms();
   if (!o.reuse_factor) {
+    if (p.split)
+      JMG_TRY(oz_prepare_a(n, A, lda, at<double>(work, p.off_ozrow), at<char>(work, p.off_ozA), s));
     JMG_TRY(launch_norm_inf(n, A, lda, c.rowsum, &c.dsc[0], s));
     JMG_TRY(launch_diag_max(n, A, lda, &c.dsc[2], s));
     JMG_CUDA(cudaMemsetAsync(&c.dsc[1], 0, sizeof(double), s));
@@ -410,7 +437,7 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
   {
     int hs3[3] = {0, 0, 0};
     JMG_TRY(sync_read(hs3, c.ints, sizeof(hs3), s));
-    if (hs3[2] != 0) return S.status = JMG_ERR_TIMEOUT;
+    if (hs3[1] != 0 || hs3[2] != 0) return S.status = JMG_ERR_TIMEOUT;
   }
   JMG_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
   JMG_TRY(launch_copy2d(n, nrhs, c.X, n, B, ldb, s));
@@ -444,6 +471,7 @@ void jmg_default_options(jmg_options* o) {
   o->shift_retry = 1;
   o->timing = 0;
   o->reuse_factor = 0;
+  o->resid = 0;
 }
 
 size_t jmg_workspace_size(int op, int n, int nrhs, int dtype, const jmg_options* opt) {
@@ -609,6 +637,51 @@ int jmg_dev_residual(int n, int nrhs, const double* A, int lda, const double* X,
   if (lwork < jmg_dev_residual_workspace(n, nrhs)) return JMG_ERR_WORKSPACE;
   return launch_residual(n, nrhs, A, lda, X, ldx, B, ldb, R, ldr, colmax, (double*)work,
                          residual_splits(n, nrhs), (cudaStream_t)stream);
+}
+
+struct SplitLayout {
+  size_t rowmax, sa, sx, part, total;
+};
+static SplitLayout split_layout(int n, int nrhs) {
+  SplitLayout L;
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    size_t at = off;
+    off = round_up(off + b, 256);
+    return at;
+  };
+  L.rowmax = take(sizeof(double) * (size_t)std::max(n, 1));
+  L.sa = take(oz_a_bytes(n));
+  L.sx = take(oz_x_bytes(n, nrhs));
+  L.part = take(sizeof(double) * (size_t)n * nrhs * oz_splits_used(n, nrhs));
+  L.total = off;
+  return L;
+}
+
+size_t jmg_dev_residual_split_workspace(int n, int nrhs) {
+  if (n <= 0 || nrhs <= 0) return 0;
+  return split_layout(n, nrhs).total;
+}
+
+int jmg_dev_residual_split(int n, int nrhs, const double* A, int lda, const double* X, int ldx,
+                           const double* B, int ldb, double* R, int ldr, double* colmax,
+                           int* err, void* work, size_t lwork, void* stream) {
+  if (n < 0) return -1;
+  if (nrhs < 0) return -2;
+  if (n == 0 || nrhs == 0) return JMG_OK;
+  if (!err) return -12;
+  const SplitLayout L = split_layout(n, nrhs);
+  if (!work || lwork < L.total) return JMG_ERR_WORKSPACE;
+  if (reinterpret_cast<uintptr_t>(work) & 255) return JMG_ERR_ALIGN;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* w = static_cast<char*>(work);
+  double* rowmax = reinterpret_cast<double*>(w + L.rowmax);
+  double* part = reinterpret_cast<double*>(w + L.part);
+  JMG_TRY(oz_prepare_a(n, A, lda, rowmax, w + L.sa, s));
+  JMG_TRY(oz_product(n, nrhs, w + L.sa, rowmax, X, ldx, w + L.sx, part, err, s));
+  JMG_CUDA(cudaMemsetAsync(colmax, 0, sizeof(double) * 3 * nrhs, s));
+  return launch_resid_reduce(n, nrhs, oz_splits_used(n, nrhs), part, X, ldx, B, ldb, R, ldr,
+                             colmax, s);
 }
 
 int jmg_dev_norm_inf(int n, const double* A, int lda, double* out, void* work, size_t lwork,

@@ -607,6 +607,14 @@ __global__ void k_resid_reduce(int n, int nrhs, int splits, const double* __rest
   }
 }
 
+int launch_resid_reduce(int n, int nrhs, int used, const double* part, const double* X, int ldx,
+                        const double* B, int ldb, double* R, int ldr, double* colmax,
+                        cudaStream_t s) {
+  dim3 grid(min(cdiv(n, 256), 64), nrhs);
+  k_resid_reduce<<<grid, 256, 0, s>>>(n, nrhs, used, part, X, ldx, B, ldb, R, ldr, colmax);
+  return launched();
+}
+
 int launch_residual(int n, int nrhs, const double* A, int lda, const double* X, int ldx,
                     const double* B, int ldb, double* R, int ldr, double* colmax, double* part,
                     int splits, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {

@@ -82,6 +82,22 @@ int launch_residual(int n, int nrhs, const double* A, int lda, const double* X, 
                     const double* B, int ldb, double* R, int ldr, double* colmax, double* part,
                     int splits, cudaStream_t s, cudaEvent_t ev0 = nullptr,
                     cudaEvent_t ev1 = nullptr);
+// R = B - sum_z part[z] (B == nullptr: R = sum_z part[z]) and the column norms
+int launch_resid_reduce(int n, int nrhs, int used, const double* part, const double* X, int ldx,
+                        const double* B, int ldb, double* R, int ldr, double* colmax,
+                        cudaStream_t s);
+
+// ---- split (Ozaki) product on the BF16 tensor cores (k_ozaki.cu)
+size_t oz_a_bytes(int n);             // slices of A
+size_t oz_x_bytes(int n, int nrhs);   // slices of X and their exponents
+int oz_splits(int n, int nrhs);       // K splits requested
+int oz_splits_used(int n, int nrhs);  // K splits the grid ends up with (partials written)
+// rowmax: n doubles; SA: oz_a_bytes(n)
+int oz_prepare_a(int n, const double* A, int lda, double* rowmax, void* SA, cudaStream_t s);
+// part[z] (z < oz_splits_used) = partial sums of A X; xwork: oz_x_bytes(n, nrhs)
+int oz_product(int n, int nrhs, const void* SA, const double* rowmax, const double* X, int ldx,
+               void* xwork, double* part, int* err, cudaStream_t s);
+
 // ||A||_inf (lower stored) into *out; rowsum: n doubles of scratch.
 int launch_norm_inf(int n, const double* A, int lda, double* rowsum, double* out,
                     cudaStream_t s);

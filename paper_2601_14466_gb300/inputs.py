@@ -39,10 +39,23 @@ def col_major(n: int, m: int, *, dtype=torch.float64, device="cpu") -> torch.Ten
     return torch.empty((m, n), dtype=dtype, device=device).t()
 
 
-def gram_shift(n: int, shift: float, seed: int = 0, device="cpu") -> torch.Tensor:
+def gram_shift(n: int, shift: float, seed: int = 0, device="cpu", fp32_product: bool = False
+               ) -> torch.Tensor:
+    """A = M M^T / n + shift I.  fp32_product draws M and forms the product in
+    FP32 (then widens to FP64): for n in the tens of thousands the FP64
+    product alone would take minutes on a GPU with slow FP64.  The matrix is
+    still exactly symmetric and, for shift >> n u_32, positive definite."""
     g = _gen(seed, device)
-    M = torch.randn((n, n), generator=g, dtype=torch.float64, device=device)
-    A = M @ M.t()
+    if fp32_product:
+        M = torch.randn((n, n), generator=g, dtype=torch.float32, device=device)
+        A32 = M @ M.t()
+        del M
+        A = A32.to(torch.float64)
+        del A32
+    else:
+        M = torch.randn((n, n), generator=g, dtype=torch.float64, device=device)
+        A = M @ M.t()
+        del M
     A.div_(n)
     A = 0.5 * (A + A.t())
     A.diagonal().add_(shift)

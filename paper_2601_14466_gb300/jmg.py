@@ -47,7 +47,7 @@ class Options(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int), ("NB", ctypes.c_int), ("prec", ctypes.c_int),
                 ("words", ctypes.c_int), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
                 ("refine", ctypes.c_int), ("shift_retry", ctypes.c_int), ("timing", ctypes.c_int),
-                ("reuse_factor", ctypes.c_int)]
+                ("reuse_factor", ctypes.c_int), ("resid", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -83,6 +83,8 @@ _SIGS = {
     "jmg_dev_syrk_fp8": (_I, [_I, _I, _I, _P, _I, _P, _P, _I, _P, _P]),
     "jmg_dev_residual_workspace": (_SZ, [_I, _I]),
     "jmg_dev_residual": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P, _SZ, _P]),
+    "jmg_dev_residual_split_workspace": (_SZ, [_I, _I]),
+    "jmg_dev_residual_split": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P, _P, _SZ, _P]),
     "jmg_dev_norm_inf": (_I, [_I, _P, _I, _P, _P, _SZ, _P]),
     "jmg_dev_probe": (_I, [_I, _I, _I, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "jmg_dev_launch_count": (ctypes.c_longlong, []),
@@ -227,7 +229,7 @@ class SolveInfo:
 def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1, nb: int = 128,
          tol: float = 1e-13, maxit: int = 50, refine: str = "auto", shift_retry: bool = True,
          overwrite_a: bool = False, work: torch.Tensor | None = None, check: bool = True,
-         timing: bool = False, reuse_factor: bool = False):
+         timing: bool = False, reuse_factor: bool = False, resid: str = "auto"):
     """Solve A X = B for SPD A (lower triangle of the column-major A read).
 
     prec "fp64": potrf + potrs in FP64 (A is overwritten with L only when
@@ -244,7 +246,8 @@ def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1
     X = colmajor_copy(B)
     o = default_options(nb=nb, prec=prec, words=words, tol=tol, maxit=maxit, refine=refine,
                         shift_retry=int(shift_retry), timing=int(timing),
-                        reuse_factor=int(reuse_factor))
+                        reuse_factor=int(reuse_factor),
+                        resid={"auto": 0, "fp64": 1, "split": 2}[resid])
     Aw = A if (overwrite_a or o.prec != 0) else colmajor_copy(A)
     pa, lda = _colmajor(Aw, "A")
     px, ldx = _colmajor(X, "B")
@@ -309,6 +312,26 @@ def residual(A: torch.Tensor, X: torch.Tensor, B: torch.Tensor):
                                  colmax.data_ptr(), work.data_ptr(), lw, _stream(A.device))
     _chk(st, "jmg_dev_residual")
     return R, colmax.view(3, nrhs)
+
+
+def residual_split(A: torch.Tensor, X: torch.Tensor, B: torch.Tensor):
+    """R = B - A X with A X from the split (Ozaki) tensor-core product; also the
+    per-column norms (r, x, b) and the device error word."""
+    _need_cuda(A, X, B)
+    n, nrhs = X.shape
+    pa, lda = _colmajor(A, "A")
+    px, ldx = _colmajor(X, "X")
+    pb, ldb = _colmajor(B, "B")
+    R = torch.empty((nrhs, n), dtype=torch.float64, device=A.device).t()
+    colmax = torch.zeros(3 * nrhs, dtype=torch.float64, device=A.device)
+    err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    lw = int(load().jmg_dev_residual_split_workspace(n, nrhs))
+    work = torch.empty(max(lw, 256), dtype=torch.uint8, device=A.device)
+    st = load().jmg_dev_residual_split(n, nrhs, pa, lda, px, ldx, pb, ldb, R.data_ptr(), n,
+                                       colmax.data_ptr(), err.data_ptr(), work.data_ptr(), lw,
+                                       _stream(A.device))
+    _chk(st, "jmg_dev_residual_split")
+    return R, colmax.view(3, nrhs), err
 
 
 def norm_inf(A: torch.Tensor) -> torch.Tensor:

@@ -213,3 +213,41 @@ def test_syrk_fp8_exact_integers(m, ncols, kext):
     touched[:, ncols:] = False
     assert np.array_equal(got[touched], want.numpy()[touched])
     assert np.array_equal(got[~touched], C0.numpy()[~touched])
+
+
+def test_syrk_tc_exact_near_fp32_limit():
+    # the split residual relies on exact FP32 accumulation of integer products
+    # up to ~2^23 in TMEM: all-maximal slices (128 * 128 * 256 = 2^22) and random ones
+    m, kext = 256, 256
+    for PA in (torch.full((m, kext), 128.0, dtype=torch.float64),
+               torch.randint(-128, 129, (m, kext), generator=torch.Generator().manual_seed(5)).double()):
+        PB = PA.clone()
+        PB[1::2] = torch.clamp(PB[1::2], -64, 64)
+        want = -(PA @ PB.t())
+        Cf = torch.zeros((m, m), dtype=torch.float32, device=DEV).t().contiguous().t()
+        err = jmg.syrk_tc_(Cf, PA.to(DEV).to(torch.bfloat16).contiguous(),
+                           PB.to(DEV).to(torch.bfloat16).contiguous())
+        torch.cuda.synchronize()
+        assert int(err.item()) == 0
+        lo = np.tril_indices(m)
+        assert np.array_equal(Cf.double().cpu().numpy()[lo], want.numpy()[lo])
+
+
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (100, 5), (300, 17), (1000, 40), (2100, 64),
+                                    (700, 3)])
+def test_residual_split_matches_dot2(n, nrhs):
+    # FP64-accurate: within the same bound as the CUDA-core FP64 residual
+    A = inputs.q_lambda(n, 1e8, seed=n) if n > 1 else inputs.gram_shift(1, 1.0, seed=1)
+    X = inputs.uniform(n, nrhs, seed=2)
+    B = inputs.rhs_from(A, X) + inputs.uniform(n, nrhs, seed=3) * 1e-6
+    Ad, _ = to_dev_colmajor(lower_only(A))
+    Xd, _ = to_dev_colmajor(X)
+    Bd, _ = to_dev_colmajor(B)
+    R, cm, err = jmg.residual_split(Ad, Xd, Bd)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    Ro = oracle.resid_dot2(A.numpy(), X.numpy(), B.numpy())
+    Af = lower_sym_full(A.numpy())
+    bound = 2 * n * U64 * (np.abs(Af) @ np.abs(X.numpy()) + np.abs(B.numpy()))
+    assert np.all(np.abs(host(R) - Ro) <= bound + 1e-300)
+    assert np.array_equal(cm.cpu().numpy()[1], np.abs(X.numpy()).max(axis=0))
