@@ -7,8 +7,8 @@
 // is scaled by 2^-eA[i] so that |a_ij| 2^-eA[i] < 1, and every column c of X
 // by 2^-eX[c]; each scaled value v is then cut into S = 8 slices of 7 bits,
 //     v = sum_s k_s 2^-7(s+1) + r,   k_s integer, |k_0| <= 128, |k_s| <= 64,
-// |r| <= 2^-57, by k_s = rint(2^7 v_s), v_{s+1} = 2^7 v_s - k_s (all exact in
-// FP64).  The integers are exact in BF16, a product of two slices is an
+// |r| <= 2^-57, as the balanced base-128 digits of the integer rint(v 2^56).
+// The integers are exact in BF16, a product of two slices is an
 // integer of at most 2^14, and
 //     (A X)_ic = 2^(eA[i] + eX[c] - 14) sum_d 2^-7d  sum_{a+b=d} sum_k A_a[i,k] X_b[k,c].
 // Pairs with a + b <= 7 are kept (the rest lie below 2^-56 of the row scale).
@@ -40,15 +40,20 @@ constexpr int ASTAGES = 4;  // ring of A-slice tiles
 constexpr int THREADS = 192;
 constexpr int A_TILE = BM * BK * 2;  // 16 KiB
 
-// slices of v (|v| < 1): k_s = rint(2^7 v_s), v_{s+1} = 2^7 v_s - k_s
-JMG_DEV void slice8(double v, __nv_bfloat16 (&out)[S]) {
+// Slices of x 2^-e (|x 2^-e| < 1): V = rint(x 2^(56-e)) is an integer with
+// |V| < 2^56 (one exact scaling and one conversion), cut into balanced base-128
+// digits from the bottom, k_s in [-64, 63] for s = 7..1, and the top digit
+// k_0 = the rest, |k_0| <= 128; then x 2^-e = sum_s k_s 2^-7(s+1) + r with
+// |r| <= 2^-57.  Integer arithmetic only after the conversion.
+JMG_DEV void slice8(double x, int e, __nv_bfloat16 (&out)[S]) {
+  long long V = __double2ll_rn(ldexp(x, 56 - e));
 #pragma unroll
-  for (int s = 0; s < S; ++s) {
-    const double t = v * 128.0;
-    const double k = rint(t);
-    out[s] = __double2bfloat16(k);  // |k| <= 128: exact
-    v = t - k;                      // exact
+  for (int s = S - 1; s >= 1; --s) {
+    const long long k = ((V + 64) & 127) - 64;
+    out[s] = __int2bfloat16_rn((int)k);  // |k| <= 64: exact
+    V = (V - k) >> 7;                    // exact
   }
+  out[0] = __int2bfloat16_rn((int)V);    // |V| <= 128: exact
 }
 
 // exponent e with |x| 2^-e < 1 for every |x| <= m (0 for m == 0)
@@ -124,7 +129,7 @@ __global__ void __launch_bounds__(256) k_oz_slice_a(int n, const double* __restr
     const int i = i0 + r, k = j0 + c;
     if (i >= n || k >= n || (diag && r < c)) continue;
     __nv_bfloat16 w[oz::S];
-    oz::slice8(ldexp(T[c][r], -er[r]), w);
+    oz::slice8(T[c][r], er[r], w);
 #pragma unroll
     for (int s = 0; s < oz::S; ++s) SA[s * sstride + (size_t)i * lds + k] = w[s];
   }
@@ -135,7 +140,7 @@ __global__ void __launch_bounds__(256) k_oz_slice_a(int n, const double* __restr
     const int row = j0 + c, k = i0 + r;
     if (row >= n || k >= n || (diag && r <= c)) continue;
     __nv_bfloat16 w[oz::S];
-    oz::slice8(ldexp(T[c][r], -ec[c]), w);
+    oz::slice8(T[c][r], ec[c], w);
 #pragma unroll
     for (int s = 0; s < oz::S; ++s) SA[s * sstride + (size_t)row * lds + k] = w[s];
   }
@@ -166,7 +171,7 @@ __global__ void __launch_bounds__(256) k_oz_slice_x(int n, int nrhs, const doubl
   if (t == 0) ex[c] = e;
   for (int k = t; k < n; k += 256) {
     __nv_bfloat16 w[oz::S];
-    oz::slice8(live ? ldexp(X[(size_t)c * ldx + k], -e) : 0.0, w);
+    oz::slice8(live ? X[(size_t)c * ldx + k] : 0.0, e, w);
 #pragma unroll
     for (int s = 0; s < oz::S; ++s) SX[s * sstride + (size_t)c * ldsx + k] = w[s];
   }
@@ -401,11 +406,23 @@ size_t oz_x_bytes(int n, int nrhs) {
   return sizeof(__nv_bfloat16) * oz::S * pad * ldsx + sizeof(int) * round_up(pad, 64);
 }
 int oz_splits(int n, int nrhs) {
+  // K splits: minimise (waves of CTAs over the SMs) x (windows per CTA), one
+  // CTA per SM (the kernel takes ~195 KB of shared memory)
   const int N = oz_n_tile(nrhs);
   const int ctas = cdiv(n, oz::BM) * cdiv(nrhs, N);
   const int nwin = cdiv(cdiv(n, oz::BK), oz::WIN);
-  int ks = std::max(1, (152 * 2 + ctas - 1) / ctas);  // about two CTAs per SM
-  return std::min(ks, nwin);
+  int best = 1;
+  long long best_cost = -1;
+  for (int ks = 1; ks <= nwin; ++ks) {
+    const int wps = cdiv(nwin, ks);
+    const int used = cdiv(nwin, wps);
+    const long long cost = (long long)cdiv(ctas * used, 152) * (wps + 1);  // +1: fixed per-CTA cost
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = ks;
+    }
+  }
+  return best;
 }
 
 int oz_prepare_a(int n, const double* A, int lda, double* rowmax, void* SA, cudaStream_t s) {
