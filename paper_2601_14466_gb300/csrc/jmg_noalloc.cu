@@ -17,11 +17,11 @@
 namespace jmg {
 namespace {
 
-// Fixed scratch: 16384 ints (64 KiB), resident on every GPU that loads the
+// Fixed scratch: 65536 ints (256 KiB), resident on every GPU that loads the
 // library until the process exits.  Every call shares it and it keeps the last
 // call's contents; the solve launcher clears the part it uses before each
 // launch.
-constexpr int kStaticScratchInts = 16384;
+constexpr int kStaticScratchInts = 65536;
 static __device__ __align__(256) int g_solve_scratch[kStaticScratchInts];
 
 // Host-side device address of g_solve_scratch, one per device, looked up on the
