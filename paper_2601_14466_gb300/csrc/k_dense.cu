@@ -13,90 +13,215 @@ namespace jmg {
 long long g_launches = 0;
 
 // ============================================================================
-// Diagonal-block factorisation L_kk L_kk^T = A_kk (kb <= 128), in place, all
-// arithmetic in FP64 (the block is held as FP64 in shared memory whatever the
-// storage type T: double for the plain path, float for the FP32 working matrix
-// of the mixed path).
+// Diagonal-block factorisation L_kk L_kk^T = A_kk (kb <= 128), in place, as a
+// blocked right-looking Cholesky over 32-column sub-blocks, one CTA:
 //
-// Right-looking with one barrier per column.  At column j every warp owns a
-// set of columns c > j (round robin) with lane = row; it forms
-// w_c = a_cj / d_j once and applies a_rc -= a_rj * w_c, which equals
-// l_rj * l_cj, to its rows r >= c.  Column j itself is only read during the
-// step, so no second barrier is needed; l_rj = a_rj / l_jj goes straight to
-// global memory.  Warp 0 updates column j+1 first and lane 0 starts the next
-// pivot (sqrt and reciprocal: exact for the plain path; FP32 seed plus one
-// Newton step of Newton's method for x^{-1/2} in the mixed path, whose output
-// is rounded to FP32 anyway) before its remaining columns, so the pivot
-// latency overlaps the update.  A pivot that is not > 0 (or NaN) records
-// info = koff + j + 1; columns before it are final, the rest keep their input.
+//  1. the 32 x 32 diagonal sub-block is factored in FP64 whatever the storage
+//     type T (double for the plain path, float for the FP32 working matrix of
+//     the mixed path).  Its 528 lower elements live in registers, three per
+//     thread; step j applies a_rc -= a_rj * a_cj / a_jj (= l_rj * l_cj) to
+//     every element with c > j, reading column j from a shared buffer that the
+//     owners of column j filled after their last update, so each column costs
+//     one barrier.  The owner of a_jj forms the pivot: sqrt and reciprocal
+//     (exact for the plain path; an FP32 seed plus one step of Newton's method
+//     for x^{-1/2} for the mixed path, whose output is rounded to FP32 anyway);
+//  2. the rows of the block below it solve x L_qq^T = a (triangular solve, one
+//     thread per row, in T);
+//  3. the rest of the block takes the symmetric rank-32 update C -= X X^T (in
+//     T, 4 x 4 register tiles).
+//
+// In the mixed path only step 1 runs in FP64: steps 2 and 3 are the panel's
+// share of the trailing update, which the tensor-core path rounds further
+// anyway, and FP64 runs at 1/64 of the FP32 rate on this GPU.  A pivot that is
+// not > 0 (or NaN) records info = koff + j + 1; the columns before it are
+// written, the rest keep their input.
 // ============================================================================
+namespace pdiag {
+constexpr int KB = 128;                  // largest diagonal block
+constexpr int BS = 32;                   // FP64 sub-block
+constexpr int TH = 256;
+constexpr int LD = KB + 4;               // shared leading dimension: 16-byte aligned columns
+constexpr int NEL = BS * (BS + 1) / 2;   // lower elements of a sub-block
+constexpr int SLOTS = (NEL + TH - 1) / TH;
+
+JMG_DEV void pivot(int j, double d, bool exact, double* s_l, double* s_il, double* s_w, int* fail,
+                   int gj) {
+  if (!(d > 0.0)) {
+    *fail = gj + 1;
+    return;
+  }
+  double l, il;
+  if (exact) {
+    l = sqrt(d);
+    il = 1.0 / l;
+  } else {
+    const double y0 = (double)rsqrtf((float)d);
+    il = y0 * fma(-0.5 * d, y0 * y0, 1.5);  // one Newton step for d^{-1/2}
+    l = d * il;
+  }
+  s_l[j] = l;
+  s_il[j] = il;
+  s_w[j] = il * il;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_potrf_diag(T* __restrict__ A, int lda, int kb, int koff,
-                                                    int* __restrict__ info) {
+JMG_DEV void load4(const T* p, T (&v)[4]);
+template <>
+JMG_DEV void load4<float>(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+}
+template <>
+JMG_DEV void load4<double>(const double* p, double (&v)[4]) {
+  const double2 q0 = reinterpret_cast<const double2*>(p)[0];
+  const double2 q1 = reinterpret_cast<const double2*>(p)[1];
+  v[0] = q0.x, v[1] = q0.y, v[2] = q1.x, v[3] = q1.y;
+}
+}  // namespace pdiag
+
+template <typename T>
+__global__ void __launch_bounds__(pdiag::TH) k_potrf_diag(T* __restrict__ A, int lda, int kb,
+                                                          int koff, int* __restrict__ info) {
+  using namespace pdiag;
   extern __shared__ __align__(16) unsigned char sm_diag[];
-  double* sa = reinterpret_cast<double*>(sm_diag);  // kb x (kb+1), column-major
-  __shared__ double s_ljj[128], s_inv[128];
+  T* sa = reinterpret_cast<T*>(sm_diag);  // kb columns, LD apart: sa[c * LD + r] = a_rc
+  __shared__ double col[2][BS];           // column j of the sub-block (double-buffered)
+  __shared__ double s_l[BS], s_il[BS], s_w[BS];
+  __shared__ T s_rinv[BS];
   __shared__ int fail;
   if (*(volatile int*)info != 0) return;  // an earlier block already failed
-  const int ld = kb + 1;
-  const int t = threadIdx.x, warp = t / 32, lane = t % 32;
   constexpr bool kExact = sizeof(T) == 8;
-  for (int base = 0; base < kb * kb; base += 256 * 16) {  // 16 independent loads per thread
+  const int t = threadIdx.x;
+  for (int base = 0; base < kb * kb; base += TH * 16) {  // 16 independent loads per thread
     T v[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const int idx = base + t + 256 * q;
+      const int idx = base + t + TH * q;
       const int i = idx % kb, j = idx / kb;
       v[q] = (idx < kb * kb && i >= j) ? A[(size_t)j * lda + i] : T(0);
     }
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const int idx = base + t + 256 * q;
-      if (idx < kb * kb) sa[(idx / kb) * ld + idx % kb] = (double)v[q];
+      const int idx = base + t + TH * q;
+      if (idx < kb * kb) sa[(idx / kb) * LD + idx % kb] = v[q];
     }
   }
-  __syncthreads();
-  auto pivot = [&](int j) {  // called by one thread once a_jj is final
-    const double d = sa[j * ld + j];
-    if (!(d > 0.0)) {
-      fail = j + 1;
-      return;
-    }
-    double l, inv;
-    if (kExact) {
-      l = sqrt(d);
-      inv = 1.0 / l;
+  // this thread's elements of a sub-block (packed column-major lower order)
+  int er[SLOTS], ec[SLOTS];
+#pragma unroll
+  for (int q = 0; q < SLOTS; ++q) {
+    int e = t + TH * q, c = 0;
+    if (e < NEL) {
+      while (e >= BS - c) e -= BS - c++;
+      er[q] = c + e;
+      ec[q] = c;
     } else {
-      const double y0 = (double)rsqrtf((float)d);
-      inv = y0 * fma(-0.5 * d, y0 * y0, 1.5);  // one Newton step for d^{-1/2}
-      l = d * inv;
+      er[q] = ec[q] = -1;
     }
-    s_ljj[j] = l;
-    s_inv[j] = inv;
-  };
-  if (t == 0) {
-    fail = 0;
-    pivot(0);
   }
+  if (t == 0) fail = 0;
   __syncthreads();
-  for (int j = 0; j < kb; ++j) {
-    if (fail) break;
-    const double inv = s_inv[j];
-    const double inv2 = inv * inv;
-    // column j of L: l_rj = a_rj / l_jj (rows j..kb-1), straight to global
-    for (int r = j + t; r < kb; r += 256) {
-      const double lrj = (r == j) ? s_ljj[j] : sa[j * ld + r] * inv;
-      A[(size_t)j * lda + r] = (T)lrj;
-    }
-    // trailing update, warp w owns columns c = j+1+w, j+1+w+8, ...
-    for (int c = j + 1 + warp; c < kb; c += 8) {
-      const double wc = sa[j * ld + c] * inv2;  // a_cj / d_j
-      int r = c + lane;
-      if (r < kb) {
-        sa[c * ld + r] -= sa[j * ld + r] * wc;
-        if (c == j + 1 && lane == 0) pivot(j + 1);  // a_{j+1,j+1} is final now
+
+  for (int p = 0; p < kb; p += BS) {
+    const int bs = min(BS, kb - p);
+    // ---- 1. FP64 factor of the sub-block
+    double a[SLOTS];
+    int cc[SLOTS];  // column of the element, -1 when it is not in the sub-block
+#pragma unroll
+    for (int q = 0; q < SLOTS; ++q) {
+      cc[q] = (ec[q] >= 0 && er[q] < bs) ? ec[q] : -1;
+      a[q] = cc[q] >= 0 ? (double)sa[(p + cc[q]) * LD + p + er[q]] : 0.0;
+      if (cc[q] == 0) {
+        col[0][er[q]] = a[q];
+        if (er[q] == 0) pivot(0, a[q], kExact, s_l, s_il, s_w, &fail, p);
       }
-      for (r += 32; r < kb; r += 32) sa[c * ld + r] -= sa[j * ld + r] * wc;
+    }
+    __syncthreads();
+    int jdone = bs;  // columns of the sub-block that are final
+    for (int j = 0; j < bs; ++j) {
+      if (fail) {
+        jdone = j;
+        break;
+      }
+      const double w = s_w[j];
+      const double* cj = col[j & 1];
+      double* cn = col[(j + 1) & 1];
+#pragma unroll
+      for (int q = 0; q < SLOTS; ++q) {
+        if (cc[q] > j) {
+          a[q] = fma(-cj[er[q]], cj[cc[q]] * w, a[q]);
+          if (cc[q] == j + 1) {
+            cn[er[q]] = a[q];
+            if (er[q] == j + 1) pivot(j + 1, a[q], kExact, s_l, s_il, s_w, &fail, p + j + 1);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    // L of the sub-block: l_cc = sqrt(a_cc), l_rc = a_rc / l_cc
+#pragma unroll
+    for (int q = 0; q < SLOTS; ++q) {
+      const int c = cc[q], r = er[q];
+      if (c >= 0 && c < jdone) {
+        const T v = (T)(r == c ? s_l[c] : a[q] * s_il[c]);
+        sa[(p + c) * LD + p + r] = v;
+        A[(size_t)(p + c) * lda + p + r] = v;
+        if (r == c) s_rinv[c] = kExact ? (T)s_il[c] : (T)__frcp_rn((float)v);
+      }
+    }
+    if (jdone < bs) break;  // (uniform: every thread read the same flag)
+    const int mr = kb - p - BS;
+    if (mr <= 0) break;
+    __syncthreads();
+
+    // ---- 2. rows below the sub-block: x L_qq^T = a, one thread per row
+    if (t < mr) {
+      const int r = p + BS + t;
+      T x[BS];
+#pragma unroll
+      for (int c = 0; c < BS; ++c) x[c] = sa[(p + c) * LD + r];
+#pragma unroll
+      for (int j = 0; j < BS; ++j) {
+        x[j] *= s_rinv[j];
+#pragma unroll
+        for (int l = j + 1; l < BS; ++l) x[l] = fma(-x[j], sa[(p + j) * LD + p + l], x[l]);
+      }
+#pragma unroll
+      for (int c = 0; c < BS; ++c) {
+        sa[(p + c) * LD + r] = x[c];
+        A[(size_t)(p + c) * lda + r] = x[c];
+      }
+    }
+    __syncthreads();
+
+    // ---- 3. trailing part of the block: C -= X X^T on 4 x 4 tiles (lower)
+    {
+      const int q0 = p + BS, nt = (mr + 3) / 4, ntiles = nt * (nt + 1) / 2;
+      for (int tile = t; tile < ntiles; tile += TH) {
+        int I = (int)((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
+        while (I * (I + 1) / 2 > tile) --I;
+        while ((I + 1) * (I + 2) / 2 <= tile) ++I;
+        const int J = tile - I * (I + 1) / 2;
+        const int r0 = q0 + 4 * I, c0 = q0 + 4 * J;
+        T acc[4][4] = {};
+#pragma unroll 8
+        for (int k = 0; k < BS; ++k) {
+          T xr[4], xc[4];
+          load4(&sa[(p + k) * LD + r0], xr);  // rows past kb read padding, never stored
+          load4(&sa[(p + k) * LD + c0], xc);
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fma(xr[i], xc[jj], acc[i][jj]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int r = r0 + i, c = c0 + jj;
+            if (r < kb && r >= c) sa[c * LD + r] -= acc[i][jj];
+          }
+      }
     }
     __syncthreads();
   }
@@ -105,15 +230,16 @@ __global__ void __launch_bounds__(256) k_potrf_diag(T* __restrict__ A, int lda, 
 
 template <typename T>
 static int potf2_impl(T* A, int lda, int kb, int koff, int* info, cudaStream_t s) {
-  size_t smem = (size_t)kb * (kb + 1) * sizeof(double);
+  if (kb > pdiag::KB) return JMG_ERR_UNSUPPORTED;
+  const size_t smem = (size_t)kb * pdiag::LD * sizeof(T);
   auto k = k_potrf_diag<T>;
   static int attr[2] = {0, 0};
   if (!attr[sizeof(T) == 8]) {
     JMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(128 * 129 * sizeof(double))));
+                                  (int)(pdiag::KB * pdiag::LD * sizeof(T))));
     attr[sizeof(T) == 8] = 1;
   }
-  k<<<1, 256, smem, s>>>(A, lda, kb, koff, info);
+  k<<<1, pdiag::TH, smem, s>>>(A, lda, kb, koff, info);
   return launched();
 }
 int launch_potf2(double* A, int lda, int kb, int koff, int* info, cudaStream_t s) {
