@@ -43,7 +43,8 @@ inline long long tri_tiles(int t) { return (long long)t * (t + 1) / 2; }
 
 // Lower-triangle tile index -> (ti, tj), ti >= tj, row-by-row enumeration.
 JMG_DEV void tri_index(int b, int& ti, int& tj) {
-  int t = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+  // FP32 estimate (FP64 is slow on this GPU), corrected to the exact integer
+  int t = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
   while ((long long)t * (t + 1) / 2 > b) --t;
   while ((long long)(t + 1) * (t + 2) / 2 <= b) ++t;
   ti = t;

@@ -22,9 +22,11 @@ long long g_launches = 0;
 //     thread; step j applies a_rc -= a_rj * a_cj / a_jj (= l_rj * l_cj) to
 //     every element with c > j, reading column j from a shared buffer that the
 //     owners of column j filled after their last update, so each column costs
-//     one barrier.  The owner of a_jj forms the pivot: sqrt and reciprocal
-//     (exact for the plain path; an FP32 seed plus one step of Newton's method
-//     for x^{-1/2} for the mixed path, whose output is rounded to FP32 anyway);
+//     one barrier.  The owner of a_jj forms 1 / a_jj, the only operation on
+//     the serial chain besides the updates (exact for the plain path; an FP32
+//     seed plus one step of Newton's method for the mixed path, whose output is
+//     rounded to FP32 anyway); sqrt(a_jj) and its reciprocal follow after the
+//     last column;
 //  2. the rows of the block below it solve x L_qq^T = a (triangular solve, one
 //     thread per row, in T);
 //  3. the rest of the block takes the symmetric rank-32 update C -= X X^T (in
@@ -44,24 +46,25 @@ constexpr int LD = KB + 4;               // shared leading dimension: 16-byte al
 constexpr int NEL = BS * (BS + 1) / 2;   // lower elements of a sub-block
 constexpr int SLOTS = (NEL + TH - 1) / TH;
 
-JMG_DEV void pivot(int j, double d, bool exact, double* s_l, double* s_il, double* s_w, int* fail,
-                   int gj) {
+// 1 / d for the updates of step j (exact division for the plain path; for the
+// mixed path an FP32 seed and one step of Newton's method for 1/d, about 44
+// bits, whose result is rounded to FP32 anyway).  Only this reciprocal sits on
+// the serial chain of the steps; sqrt(d) is taken after the last step.
+JMG_DEV void pivot(int j, double d, bool exact, double* s_w, int* fail, int gj) {
   if (!(d > 0.0)) {
     *fail = gj + 1;
     return;
   }
-  double l, il;
-  if (exact) {
-    l = sqrt(d);
-    il = 1.0 / l;
+  double w;
+  if (exact || d < 1e-30) {  // (below the FP32 normal range the seed is useless)
+    w = 1.0 / d;
   } else {
-    const double y0 = (double)rsqrtf((float)d);
-    il = y0 * fma(-0.5 * d, y0 * y0, 1.5);  // one Newton step for d^{-1/2}
-    l = d * il;
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"((float)d));
+    const double y0 = (double)y;
+    w = fma(y0, fma(-d, y0, 1.0), y0);
   }
-  s_l[j] = l;
-  s_il[j] = il;
-  s_w[j] = il * il;
+  s_w[j] = w;
 }
 
 template <typename T>
@@ -133,7 +136,7 @@ __global__ void __launch_bounds__(pdiag::TH) k_potrf_diag(T* __restrict__ A, int
       a[q] = cc[q] >= 0 ? (double)sa[(p + cc[q]) * LD + p + er[q]] : 0.0;
       if (cc[q] == 0) {
         col[0][er[q]] = a[q];
-        if (er[q] == 0) pivot(0, a[q], kExact, s_l, s_il, s_w, &fail, p);
+        if (er[q] == 0) pivot(0, a[q], kExact, s_w, &fail, p);
       }
     }
     __syncthreads();
@@ -152,13 +155,31 @@ __global__ void __launch_bounds__(pdiag::TH) k_potrf_diag(T* __restrict__ A, int
           a[q] = fma(-cj[er[q]], cj[cc[q]] * w, a[q]);
           if (cc[q] == j + 1) {
             cn[er[q]] = a[q];
-            if (er[q] == j + 1) pivot(j + 1, a[q], kExact, s_l, s_il, s_w, &fail, p + j + 1);
+            if (er[q] == j + 1) pivot(j + 1, a[q], kExact, s_w, &fail, p + j + 1);
           }
         }
       }
       __syncthreads();
     }
     // L of the sub-block: l_cc = sqrt(a_cc), l_rc = a_rc / l_cc
+#pragma unroll
+    for (int q = 0; q < SLOTS; ++q) {
+      const int c = cc[q];
+      if (c >= 0 && c < jdone && er[q] == c) {
+        double l, il;
+        if (kExact || a[q] < 1e-30) {
+          l = sqrt(a[q]);
+          il = 1.0 / l;
+        } else {
+          const double y0 = (double)rsqrtf((float)a[q]);
+          il = y0 * fma(-0.5 * a[q], y0 * y0, 1.5);  // one Newton step for d^{-1/2}
+          l = a[q] * il;
+        }
+        s_l[c] = l;
+        s_il[c] = il;
+      }
+    }
+    __syncthreads();
 #pragma unroll
     for (int q = 0; q < SLOTS; ++q) {
       const int c = cc[q], r = er[q];

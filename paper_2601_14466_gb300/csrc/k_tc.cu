@@ -8,13 +8,19 @@
 // the pairs (hi*hi, hi*lo, lo*hi, ...) are concatenated along K, so one GEMM with
 // K' = pairs * kb applies all of them to the same FP32 accumulator.
 //
-// One CTA per 128 x 128 output tile, 128 threads:
+// Persistent: one CTA per SM walks the 128 x 128 output tiles of the lower
+// trapezoid, 320 threads:
 //   warp 0 (one lane): TMA producer -- 128 x 64 tiles of PA and PB per stage,
 //                       128-byte swizzle, mbarrier transaction counts;
-//   warp 1 (one lane): MMA issuer   -- tcgen05.mma kind::f16, M=128 N=128 K=16,
-//                       FP32 accumulator in TMEM (128 lanes x 128 columns);
-//   all 4 warps:       epilogue     -- tcgen05.ld 32 lanes x 32 columns, then
-//                       C -= acc with coalesced column accesses (lane = row).
+//   warp 1 (one lane): MMA issuer   -- tcgen05.mma kind::f16, M=128 N=128 K=16
+//                       (or kind::f8f6f4, K=32), FP32 accumulators in TMEM, two
+//                       of them so the MMAs of the next tile overlap the
+//                       epilogue of this one;
+//   warps 2-9:         epilogue     -- tcgen05.ld 32 lanes x 32 columns, then
+//                       C -= acc with coalesced column accesses (lane = row);
+//                       two warps per TMEM lane quarter, 64 columns each.  They
+//                       prefetch the next tile's C into L2 before they drain
+//                       this one, so the read-modify-write of C meets L2.
 // Every mbarrier wait is bounded (globaltimer); on expiry the kernel raises
 // *err, drains its own copies, frees TMEM and returns without touching C.
 //
@@ -46,14 +52,16 @@ JMG_DEV void trap_index(int b, int TJ, int& ti, int& tj) {
 }
 
 
-// Persistent, warp-specialised update.  192 threads:
+// Persistent, warp-specialised update.  320 threads:
 //   warp 0: TMA producer (one lane), warp 1: MMA issuer (one lane),
-//   warps 2-5: epilogue; warp w reads TMEM lanes 32 (w % 4) .. +31.
+//   warps 2-9: epilogue; warp w reads TMEM lanes 32 (w % 4) .. +31, columns
+//   64 ((w - 2) / 4) .. +63 of the accumulator.
 // Two TMEM accumulators (2 x 128 columns): the MMAs of tile i+1 run while the
 // epilogue drains tile i.  Barriers: full/empty per smem stage, acc_full /
 // acc_empty per accumulator.
 constexpr int PSTAGES = 6;
-constexpr int PTHREADS = 192;
+constexpr int PTHREADS = 320;
+constexpr int EPI_WARPS = 8;
 constexpr int PSMEM_BYTES = PSTAGES * STAGE_BYTES + 1024 + 512;
 constexpr uint32_t PTMEM_COLS = 256;
 
@@ -89,7 +97,7 @@ __global__ void __launch_bounds__(PTHREADS, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&acc_full[a], 1);
-      mbar_init(&acc_empty[a], 4);
+      mbar_init(&acc_empty[a], EPI_WARPS);
     }
     fence_mbar_init();
     prefetch_tmap(&tmA);
@@ -170,12 +178,29 @@ __global__ void __launch_bounds__(PTHREADS, 1)
       }
     }
   } else {
-    // epilogue warps 2..5
-    const int q = warp & 3;  // TMEM lane group of this warp
+    // epilogue warps 2..9
+    const int q = warp & 3;                    // TMEM lane group of this warp
+    const int ch = ((warp - 2) / 4) * (BN / 2);  // its half of the columns
+    const int e = (warp - 2) * 32 + lane;      // 0..255: prefetch duty
+    // L2 prefetch of the C tile (ti, tj): column e % 128, two 32-row lines
+    auto prefetch_c = [&](int b) {
+      if (b >= ntiles) return;
+      int pi, pj;
+      trap_index(b, TJ, pi, pj);
+      const int c = pj * BN + (e % BN);
+      if (c >= ncols) return;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = pi * BM + ((e / BN) * 2 + h) * 32;
+        if (r < m) asm volatile("prefetch.global.L2 [%0];" ::"l"(C + (size_t)c * ldc + r));
+      }
+    };
+    prefetch_c(blockIdx.x);
     int i = 0;
     for (int b = blockIdx.x; b < ntiles; b += gridDim.x, ++i) {
       int ti, tj;
       trap_index(b, TJ, ti, tj);
+      prefetch_c(b + gridDim.x);
       const int a = i & 1;
       const bool ok = mbar_wait(&acc_full[a], (uint32_t)(i / 2) & 1);
       tc_fence_after();
@@ -187,26 +212,22 @@ __global__ void __launch_bounds__(PTHREADS, 1)
       const bool diag = (ti == tj);
       const float scale = (KIND == 1) ? exp2f(-(float)((int)exps[ti] + (int)exps[tj])) : 1.0f;
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      for (int c0 = ch; c0 < ch + BN / 2; c0 += 32) {
         uint32_t v[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN + c0), v);
         tmem_ld_wait();
         if (r < m) {
           // all 32 loads first (independent, coalesced across the warp), then the stores
-          float* cp = C + r;
           const int cb = tj * BN + c0;
+          float* cp = C + (size_t)cb * ldc + r;
+          // columns j < jn of this chunk are in range (and on or below the diagonal)
+          const int jn = min(32, min(ncols - cb, diag ? r - cb + 1 : 32));
           float old[32];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int c = cb + j;
-            old[j] = (c < ncols && (!diag || r >= c)) ? cp[(size_t)c * ldc] : 0.0f;
-          }
+          for (int j = 0; j < 32; ++j) old[j] = j < jn ? cp[j * ldc] : 0.0f;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int c = cb + j;
-            if (c < ncols && (!diag || r >= c))
-              cp[(size_t)c * ldc] = old[j] - scale * __uint_as_float(v[j]);
-          }
+          for (int j = 0; j < 32; ++j)
+            if (j < jn) cp[j * ldc] = old[j] - scale * __uint_as_float(v[j]);
         }
       }
       tc_fence_before();
