@@ -334,9 +334,14 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
 
   const double t0 = now_ms();
   if (!o.reuse_factor) {
-    if (p.split)
-      JMG_TRY(oz_prepare_a(n, A, lda, at<double>(work, p.off_ozrow), at<char>(work, p.off_ozA), s));
-    JMG_TRY(launch_norm_inf(n, A, lda, c.rowsum, &c.dsc[0], s));
+    if (p.split) {  // one pass for the row sums (||A||_inf) and row maxima (slice scales)
+      double* rowmax = at<double>(work, p.off_ozrow);
+      JMG_TRY(launch_row_stats(n, A, lda, c.rowsum, rowmax, s));
+      JMG_TRY(launch_max_reduce(n, c.rowsum, &c.dsc[0], s));
+      JMG_TRY(oz_slice_a(n, A, lda, rowmax, at<char>(work, p.off_ozA), s));
+    } else {
+      JMG_TRY(launch_norm_inf(n, A, lda, c.rowsum, &c.dsc[0], s));
+    }
     JMG_TRY(launch_diag_max(n, A, lda, &c.dsc[2], s));
     JMG_CUDA(cudaMemsetAsync(&c.dsc[1], 0, sizeof(double), s));
   }

@@ -779,44 +779,106 @@ int launch_residual(int n, int nrhs, const double* A, int lda, const double* X, 
   return launched();
 }
 
-// ||A||_inf from lower(A): each 64 x 64 lower tile adds |a_ij| to row i and,
-// below the diagonal, to row j (the mirrored entry).
-__global__ void k_rowsum_lower(int n, const double* __restrict__ A, int lda,
-                               double* __restrict__ rowsum) {
-  int ti, tj;
-  tri_index(blockIdx.x, ti, tj);
-  const int i0 = ti * 64, j0 = tj * 64;
-  const int tx = threadIdx.x % 64, ty = threadIdx.x / 64;  // 256 threads
-  const int i = i0 + tx;
-  double rs = 0.0;
-  double cs[16];
+// Row statistics of the symmetric A from its lower triangle:
+//   rowsum[i] = sum_j |a_ij|   (NaN propagates; ||A||_inf = max_i rowsum[i])
+//   rowmax[i] = max_j |a_ij| truncated to its upper 32 bits (sign, exponent
+//               and 20 leading fraction bits): the same binary exponent as the
+//               maximum, which is all the row scales of the split residual use
+// over the full row j = 0..n-1.  One CTA per strip of 32 columns j reads them
+// down from the diagonal in 1024-row chunks (long contiguous runs of each
+// column, 16 loads in flight per thread).  Entry a_rj (r > j) adds to row r --
+// kept per thread for its four rows of the chunk and flushed with one atomic
+// per row and chunk -- and to row j (its mirror), kept per thread for the
+// strip's 32 columns and reduced across the CTA at the end; a_jj adds once.
+// The maxima are taken on the upper 32 bits of |a| as unsigned integers,
+// which order like the values (NaN above every finite value).
+__global__ void __launch_bounds__(256, 1) k_row_stats(int n, const double* __restrict__ A,
+                                                      int lda, double* __restrict__ rowsum,
+                                                      double* __restrict__ rowmax) {
+  constexpr int W = 32, U = 4, TH = 256, JB = 4;
+  __shared__ double red_s[TH / 32][W];
+  __shared__ unsigned red_m[TH / 32][W];
+  const int j0 = blockIdx.x * W;
+  const int jn = min(W, n - j0);
+  const int t = threadIdx.x, lane = t % 32, warp = t / 32;
+  double cs[W];
+  unsigned cm[W];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) cs[q] = 0.0;
+  for (int jj = 0; jj < W; ++jj) cs[jj] = 0.0, cm[jj] = 0u;
+  for (int rb = j0; rb < n; rb += TH * U) {
+    double rs[U];
+    unsigned rm[U];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    int j = j0 + ty * 16 + q;
-    if (i < n && j < n && i >= j) {
-      double v = fabs(A[(size_t)j * lda + i]);
-      rs += v;
-      if (i > j) cs[q] = v;
+    for (int u = 0; u < U; ++u) rs[u] = 0.0, rm[u] = 0u;
+    const double* base = A + (size_t)j0 * lda + rb + t;  // (column j0, row rb + t)
+#pragma unroll
+    for (int jb = 0; jb < W; jb += JB) {
+      double v[JB][U];
+#pragma unroll
+      for (int q = 0; q < JB; ++q)  // JB x U independent loads
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int j = j0 + jb + q, r = rb + t + TH * u;
+          v[q][u] = (jb + q < jn && r >= j && r < n) ? fabs(base[(jb + q) * lda + TH * u]) : 0.0;
+        }
+#pragma unroll
+      for (int q = 0; q < JB; ++q)
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int j = j0 + jb + q, r = rb + t + TH * u;
+          const unsigned hi = (unsigned)__double2hiint(v[q][u]);
+          rs[u] += v[q][u];
+          rm[u] = max(rm[u], hi);
+          if (r > j) {
+            cs[jb + q] += v[q][u];
+            cm[jb + q] = max(cm[jb + q], hi);
+          }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = rb + t + TH * u;
+      if (r < n) {
+        if (rowsum) atomicAdd(&rowsum[r], rs[u]);
+        if (rowmax) atomicMax(reinterpret_cast<unsigned*>(&rowmax[r]) + 1, rm[u]);
+      }
     }
   }
-  if (i < n) atomicAdd(&rowsum[i], rs);
-  // column sums over the 64 rows: reduce cs[q] across tx (64 threads = 2 warps)
+  // the mirrored part of rows j0 .. j0+31: reduce the column sums over the CTA
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    double v = cs[q];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    cs[q] = v;
-  }
-  // lane 0 of each warp adds the partial column sums of its 32 rows
-  if ((tx & 31) == 0) {
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      int j = j0 + ty * 16 + q;
-      if (j < n && cs[q] != 0.0) atomicAdd(&rowsum[j], cs[q]);
+  for (int jj = 0; jj < W; ++jj) {
+    double a = cs[jj];
+    unsigned m = cm[jj];
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if (lane == jj) {
+      red_s[warp][jj] = a;
+      red_m[warp][jj] = m;
     }
   }
+  __syncthreads();
+  if (t < jn) {
+    double a = 0.0;
+    unsigned m = 0u;
+#pragma unroll
+    for (int w = 0; w < TH / 32; ++w) {
+      a += red_s[w][t];
+      m = max(m, red_m[w][t]);
+    }
+    if (rowsum) atomicAdd(&rowsum[j0 + t], a);
+    if (rowmax) atomicMax(reinterpret_cast<unsigned*>(&rowmax[j0 + t]) + 1, m);
+  }
+}
+
+int launch_row_stats(int n, const double* A, int lda, double* rowsum, double* rowmax,
+                     cudaStream_t s) {
+  if (n <= 0) return JMG_OK;
+  if (rowsum) JMG_CUDA(cudaMemsetAsync(rowsum, 0, sizeof(double) * n, s));
+  if (rowmax) JMG_CUDA(cudaMemsetAsync(rowmax, 0, sizeof(double) * n, s));
+  k_row_stats<<<cdiv(n, 32), 256, 0, s>>>(n, A, lda, rowsum, rowmax);
+  return launched();
 }
 
 __global__ void k_max_reduce(int n, const double* __restrict__ v, double* __restrict__ out) {
@@ -830,15 +892,17 @@ __global__ void k_max_reduce(int n, const double* __restrict__ v, double* __rest
   if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
 }
 
-int launch_norm_inf(int n, const double* A, int lda, double* rowsum, double* out,
-                    cudaStream_t s) {
+int launch_max_reduce(int n, const double* v, double* out, cudaStream_t s) {
   JMG_CUDA(cudaMemsetAsync(out, 0, sizeof(double), s));
   if (n <= 0) return JMG_OK;
-  JMG_CUDA(cudaMemsetAsync(rowsum, 0, sizeof(double) * n, s));
-  k_rowsum_lower<<<(unsigned)tri_tiles(cdiv(n, 64)), 256, 0, s>>>(n, A, lda, rowsum);
-  JMG_TRY(launched());
-  k_max_reduce<<<min(cdiv(n, 256), 152), 256, 0, s>>>(n, rowsum, out);
+  k_max_reduce<<<min(cdiv(n, 256), 152), 256, 0, s>>>(n, v, out);
   return launched();
+}
+
+int launch_norm_inf(int n, const double* A, int lda, double* rowsum, double* out,
+                    cudaStream_t s) {
+  JMG_TRY(launch_row_stats(n, A, lda, rowsum, nullptr, s));
+  return launch_max_reduce(n, rowsum, out, s);
 }
 
 __global__ void k_eta(int nrhs, const double* __restrict__ colmax, const double* __restrict__ anorm,

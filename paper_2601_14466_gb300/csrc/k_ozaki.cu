@@ -15,16 +15,17 @@
 // For each d the inner sums are accumulated on the tensor cores in FP32 in a
 // TMEM accumulator of its own; over a window of 256 values of k every partial
 // sum is an integer below 2^24 (at most 2.5 * 2^14 * 256), so it is exact.
-// After each window the epilogue adds the 8 accumulators into FP64 registers
-// (d = 0..3 in FP64; d = 4..7 first in FP32, whose rounding is below 2^-52 of
-// the result), and at the end scales by the powers of two and stores one FP64
-// partial sum per K split.  R = B - sum of partials is formed by the same
+// After each window the epilogue converts the 8 accumulators to integers and
+// adds them, exactly, into two 64-bit sums per output (d = 0..3 and d = 4..7,
+// each weighted by its power of 2^7); at the end the two sums become one FP64
+// value (one rounding), scaled by the powers of two, and one FP64 partial sum
+// per K split is stored.  R = B - sum of partials is formed by the same
 // reduction kernel as the CUDA-core residual.
 //
-// tcgen05 kernel, 192 threads: warp 0 issues TMA loads (8 X-slice tiles per
+// tcgen05 kernel, 320 threads: warp 0 issues TMA loads (8 X-slice tiles per
 // 64-wide K block, then 8 A-slice tiles through a 4-stage ring), warp 1 issues
-// the MMAs (M = 128, N = 16/32/64, K = 16; 144 per K block), warps 2-5 drain
-// TMEM.  All waits are bounded.
+// the MMAs (M = 128, N = 16/32/64, K = 16; 144 per K block), warps 2-9 drain
+// TMEM (two per TMEM lane quarter).  All waits are bounded.
 #include <algorithm>
 
 #include "kernels.h"
@@ -37,16 +38,47 @@ constexpr int BM = 128;     // rows per tile
 constexpr int BK = 64;      // K per block: 64 BF16 = one 128-byte swizzle row
 constexpr int WIN = 4;      // K blocks per exact accumulation window (256 values)
 constexpr int ASTAGES = 4;  // ring of A-slice tiles
-constexpr int THREADS = 192;
+constexpr int THREADS = 320;  // warps 0-1 producer / MMA, 2-9 epilogue
 constexpr int A_TILE = BM * BK * 2;  // 16 KiB
 
+// rint(x 2^(56-e)) for |x| < 2^e, formed from the bits of x with integer
+// operations only (FP64 runs at 1/64 of the FP32 rate on this GPU): x is
+// M 2^(ex-1075) with the 53-bit significand M, so the value is M 2^sh with
+// sh = ex - 1019 - e <= 3, a left shift, or a right shift rounded to nearest
+// with ties to even.  Non-finite x gives 0 (those rows carry no valid slices).
+JMG_DEV long long scaled_int(double x, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0x7FF) return 0;
+  unsigned long long M = b & ((1ull << 52) - 1);
+  int ee = ex;
+  if (ex)
+    M |= 1ull << 52;
+  else
+    ee = 1;  // subnormal
+  const int sh = ee - 1019 - e;
+  unsigned long long V;
+  if (sh >= 0) {
+    V = (sh > 62 || (M >> (62 - sh)) != 0) ? 0ull : M << sh;  // (no overflow when |x| < 2^e)
+  } else {
+    const int k = -sh;
+    if (k >= 64) {
+      V = 0;
+    } else {
+      V = M >> k;
+      const unsigned long long rem = M & ((1ull << k) - 1), half = 1ull << (k - 1);
+      if (rem > half || (rem == half && (V & 1))) ++V;
+    }
+  }
+  return (b >> 63) ? -(long long)V : (long long)V;
+}
+
 // Slices of x 2^-e (|x 2^-e| < 1): V = rint(x 2^(56-e)) is an integer with
-// |V| < 2^56 (one exact scaling and one conversion), cut into balanced base-128
-// digits from the bottom, k_s in [-64, 63] for s = 7..1, and the top digit
-// k_0 = the rest, |k_0| <= 128; then x 2^-e = sum_s k_s 2^-7(s+1) + r with
-// |r| <= 2^-57.  Integer arithmetic only after the conversion.
+// |V| < 2^56, cut into balanced base-128 digits from the bottom, k_s in
+// [-64, 63] for s = 7..1, and the top digit k_0 = the rest, |k_0| <= 128; then
+// x 2^-e = sum_s k_s 2^-7(s+1) + r with |r| <= 2^-57.  Integer arithmetic only.
 JMG_DEV void slice8(double x, int e, __nv_bfloat16 (&out)[S]) {
-  long long V = __double2ll_rn(ldexp(x, 56 - e));
+  long long V = scaled_int(x, e);
 #pragma unroll
   for (int s = S - 1; s >= 1; --s) {
     const long long k = ((V + 64) & 127) - 64;
@@ -65,43 +97,9 @@ JMG_DEV int scale_exp(double m) {
 }
 }  // namespace oz
 
-// ---------------------------------------------------------------------------
-// row maxima of |A| for the symmetric matrix held in lower(A)
-__global__ void k_oz_rowmax(int n, const double* __restrict__ A, int lda,
-                            double* __restrict__ rowmax) {
-  int ti, tj;
-  tri_index(blockIdx.x, ti, tj);
-  const int i0 = ti * 64, j0 = tj * 64;
-  const int tx = threadIdx.x % 64, ty = threadIdx.x / 64;  // 256 threads
-  const int i = i0 + tx;
-  double rm = 0.0;
-  double cm[16];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int j = j0 + ty * 16 + q;
-    double v = 0.0;
-    if (i < n && j < n && i >= j) v = fabs(A[(size_t)j * lda + i]);
-    rm = fmax(rm, v);
-    cm[q] = v;
-  }
-  if (i < n) atomic_max_nonneg(&rowmax[i], rm);
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    double v = cm[q];
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    cm[q] = v;
-  }
-  if ((tx & 31) == 0) {
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int j = j0 + ty * 16 + q;
-      if (j < n && cm[q] > 0.0) atomic_max_nonneg(&rowmax[j], cm[q]);
-    }
-  }
-}
-
 // A slices: SA[s * sstride + i * lds + k] for every (i, k) of the symmetric
-// matrix.  One CTA per lower 64 x 64 tile writes the tile and its mirror.
+// matrix.  One CTA per lower 64 x 64 tile writes the tile and its mirror; each
+// thread cuts 4 consecutive values of a row and stores 8 bytes per slice.
 __global__ void __launch_bounds__(256) k_oz_slice_a(int n, const double* __restrict__ A, int lda,
                                                     const double* __restrict__ rowmax,
                                                     __nv_bfloat16* __restrict__ SA, int lds,
@@ -112,37 +110,68 @@ __global__ void __launch_bounds__(256) k_oz_slice_a(int n, const double* __restr
   __shared__ double T[64][65];  // T[c][r] = a(i0 + r, j0 + c)
   __shared__ int er[64], ec[64];
   const int t = threadIdx.x;
-  for (int q = 0; q < 16; ++q) {
-    const int idx = t + 256 * q;
-    const int r = idx % 64, c = idx / 64;
-    const int i = i0 + r, j = j0 + c;
-    T[c][r] = (i < n && j < n && i >= j) ? A[(size_t)j * lda + i] : 0.0;
+  {
+    double v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {  // all loads first
+      const int idx = t + 256 * q;
+      const int r = idx % 64, c = idx / 64;
+      const int i = i0 + r, j = j0 + c;
+      v[q] = (i < n && j < n && i >= j) ? A[(size_t)j * lda + i] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int idx = t + 256 * q;
+      T[idx / 64][idx % 64] = v[q];
+    }
   }
   if (t < 64) er[t] = (i0 + t < n) ? oz::scale_exp(rowmax[i0 + t]) : 0;
   else if (t < 128) ec[t - 64] = (j0 + t - 64 < n) ? oz::scale_exp(rowmax[j0 + t - 64]) : 0;
   __syncthreads();
   const bool diag = ti == tj;
-  // direct: row i = i0 + r, column k = j0 + c; threads run along k
-  for (int q = 0; q < 16; ++q) {
+  // the row of the padded slice ends at lds (a multiple of 64): 4-wide groups
+  // never straddle it; values past n or above the diagonal are zero
+  auto put4 = [&](int row, int k, const double (&x)[4], int e) {
+    __nv_bfloat16 w[4][oz::S];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) oz::slice8(x[u], e, w[u]);
+#pragma unroll
+    for (int s = 0; s < oz::S; ++s) {
+      __nv_bfloat162 lo, hi;
+      lo.x = w[0][s], lo.y = w[1][s], hi.x = w[2][s], hi.y = w[3][s];
+      uint2 pk;
+      pk.x = *reinterpret_cast<uint32_t*>(&lo);
+      pk.y = *reinterpret_cast<uint32_t*>(&hi);
+      *reinterpret_cast<uint2*>(&SA[s * sstride + (size_t)row * lds + k]) = pk;
+    }
+  };
+  // direct: row i = i0 + r, columns k = j0 + c .. c+3 (threads run along k).
+  // On a diagonal tile the whole row segment is written here, the entries
+  // above the diagonal from their mirrors (a_rk = a_kr).
+#pragma unroll 1
+  for (int q = 0; q < 4; ++q) {
     const int idx = t + 256 * q;
-    const int c = idx % 64, r = idx / 64;
+    const int c = 4 * (idx % 16), r = idx / 16;
     const int i = i0 + r, k = j0 + c;
-    if (i >= n || k >= n || (diag && r < c)) continue;
-    __nv_bfloat16 w[oz::S];
-    oz::slice8(T[c][r], er[r], w);
+    if (i >= n || k >= n) continue;
+    double x[4];  // (zero past n)
 #pragma unroll
-    for (int s = 0; s < oz::S; ++s) SA[s * sstride + (size_t)i * lds + k] = w[s];
+    for (int u = 0; u < 4; ++u) x[u] = (!diag || c + u <= r) ? T[c + u][r] : T[r][c + u];
+    put4(i, k, x, er[r]);
   }
-  // mirror: row j0 + c, column i0 + r (strictly above the diagonal); threads run along r
-  for (int q = 0; q < 16; ++q) {
+  if (diag) return;
+  // mirror: row j0 + c, columns k = i0 + r .. r+3 (the tile is strictly below
+  // the diagonal, so its transpose is strictly above it)
+#pragma unroll 1
+  for (int q = 0; q < 4; ++q) {
     const int idx = t + 256 * q;
-    const int r = idx % 64, c = idx / 64;
+    const int r = 4 * (idx % 16), c = idx / 16;
     const int row = j0 + c, k = i0 + r;
-    if (row >= n || k >= n || (diag && r <= c)) continue;
-    __nv_bfloat16 w[oz::S];
-    oz::slice8(T[c][r], ec[c], w);
+    if (row >= n || k >= n) continue;
+    double x[4];
 #pragma unroll
-    for (int s = 0; s < oz::S; ++s) SA[s * sstride + (size_t)row * lds + k] = w[s];
+    for (int u = 0; u < 4; ++u) x[u] = T[c][r + u];
+    put4(row, k, x, ec[c]);
   }
 }
 
@@ -224,7 +253,7 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
       mbar_init(&aempty[i], 1);
     }
     mbar_init(accf, 1);
-    mbar_init(acce, 4);
+    mbar_init(acce, N == 16 ? 4 : 8);
     fence_mbar_init();
     prefetch_tmap(&tmA);
     prefetch_tmap(&tmX);
@@ -317,62 +346,68 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
       if (!ok) atomicExch(&s_fail, 1);
     }
   } else {
-    // epilogue: warps 2-5, TMEM lane group q = warp % 4 -> rows rt*128 + 32q + lane
+    // epilogue: warp w reads TMEM lane group q = w % 4 (rows rt*128 + 32q + lane)
+    // and CW columns of the accumulators.  Every window's accumulators are exact
+    // integers (below 2^24); they are converted to integers and summed exactly
+    // in 64 bits, d = 0..3 as hs = sum acc_d 2^(21-7d) and d = 4..7 as
+    // ls = sum acc_d 2^(49-7d) (each window adds less than 2^45 to either, and
+    // a CTA takes at most 256 windows, so both stay below 2^53).  Only the end
+    // converts to FP64: sum_d acc_d 2^-7d = 2^-21 (hs + ls 2^-28), one rounding.
+    constexpr int EW = (N == 16) ? 4 : 8;  // epilogue warps with columns
+    constexpr int CW = N * 4 / EW;         // columns per epilogue warp (16 or 32)
+    const int ew = warp - 2;
     const int q = warp & 3;
-    double tot[N];
+    const int ch = (ew >> 2) * CW;
+    if (ew < EW) {
+      unsigned long long hs[CW], ls[CW];  // (unsigned: garbage rows past n wrap, never trap)
 #pragma unroll
-    for (int c = 0; c < N; ++c) tot[c] = 0.0;
-    bool ok = true;
-    for (int w = w0; w < w1; ++w) {
-      if (!mbar_wait(accf, (uint32_t)((w - w0) & 1)) || *(volatile int*)&s_fail) {
-        ok = false;
-        break;
-      }
-      tc_fence_after();
-#pragma unroll
-      for (int c0 = 0; c0 < N; c0 += 16) {
-        float lo[16];
-#pragma unroll
-        for (int c = 0; c < 16; ++c) lo[c] = 0.0f;
-        // d = 7 .. 4 in FP32 (Horner in 2^-7), then d = 3 .. 0 in FP64
-#pragma unroll
-        for (int d = S - 1; d >= 4; --d) {
-          uint32_t v[16];
-          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * N + c0), v);
-          tmem_ld_wait();
-#pragma unroll
-          for (int c = 0; c < 16; ++c) lo[c] = fmaf(lo[c], 0.0078125f, __uint_as_float(v[c]));
+      for (int c = 0; c < CW; ++c) hs[c] = ls[c] = 0ull;
+      bool ok = true;
+      for (int w = w0; w < w1; ++w) {
+        if (!mbar_wait(accf, (uint32_t)((w - w0) & 1)) || *(volatile int*)&s_fail) {
+          ok = false;
+          break;
         }
+        tc_fence_after();
 #pragma unroll
-        for (int d = 3; d >= 0; --d) {
-          uint32_t v[16];
-          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * N + c0), v);
-          tmem_ld_wait();
-          const double sd = ldexp(1.0, -7 * d);
+        for (int d = 0; d < S; ++d) {
+          const long long sc = 1ll << (d <= 3 ? 21 - 7 * d : 49 - 7 * d);
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            if (d == 3) tot[c0 + c] = fma((double)lo[c], ldexp(1.0, -28), tot[c0 + c]);
-            tot[c0 + c] = fma((double)__uint_as_float(v[c]), sd, tot[c0 + c]);
+          for (int c0 = 0; c0 < CW; c0 += 16) {
+            uint32_t v[16];
+            tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * N + ch + c0), v);
+            tmem_ld_wait();
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              const long long t = (long long)__float2int_rn(__uint_as_float(v[c])) * sc;
+              if (d <= 3)
+                hs[c0 + c] += (unsigned long long)t;
+              else
+                ls[c0 + c] += (unsigned long long)t;
+            }
           }
         }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acce);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(acce);
-    }
-    if (ok) {
-      const int row = rt * BM + q * 32 + lane;
-      if (row < n) {
-        const int er = oz::scale_exp(rowmax[row]);
+      if (ok) {
+        const int row = rt * BM + q * 32 + lane;
+        if (row < n) {
+          const int er = oz::scale_exp(rowmax[row]);
 #pragma unroll
-        for (int c = 0; c < N; ++c) {
-          const int col = ct * N + c;
-          if (col < nrhs)
-            part[(size_t)z * n * nrhs + (size_t)col * n + row] = ldexp(tot[c], er + ex[col] - 14);
+          for (int c = 0; c < CW; ++c) {
+            const int col = ct * N + ch + c;
+            if (col < nrhs) {
+              const double tot = fma((double)(long long)ls[c], 0x1p-28, (double)(long long)hs[c]);
+              part[(size_t)z * n * nrhs + (size_t)col * n + row] =
+                  ldexp(tot, er + ex[col] - 14 - 21);
+            }
+          }
         }
+      } else {
+        atomicExch(&s_fail, 1);
       }
-    } else {
-      atomicExch(&s_fail, 1);
     }
   }
   __syncwarp();
@@ -411,9 +446,9 @@ int oz_splits(int n, int nrhs) {
   const int N = oz_n_tile(nrhs);
   const int ctas = cdiv(n, oz::BM) * cdiv(nrhs, N);
   const int nwin = cdiv(cdiv(n, oz::BK), oz::WIN);
-  int best = 1;
+  int best = cdiv(nwin, 256);
   long long best_cost = -1;
-  for (int ks = 1; ks <= nwin; ++ks) {
+  for (int ks = cdiv(nwin, 256); ks <= nwin; ++ks) {  // at most 256 windows per CTA
     const int wps = cdiv(nwin, ks);
     const int used = cdiv(nwin, wps);
     const long long cost = (long long)cdiv(ctas * used, 152) * (wps + 1);  // +1: fixed per-CTA cost
@@ -426,11 +461,13 @@ int oz_splits(int n, int nrhs) {
 }
 
 int oz_prepare_a(int n, const double* A, int lda, double* rowmax, void* SA, cudaStream_t s) {
+  JMG_TRY(launch_row_stats(n, A, lda, nullptr, rowmax, s));
+  return oz_slice_a(n, A, lda, rowmax, SA, s);
+}
+
+int oz_slice_a(int n, const double* A, int lda, const double* rowmax, void* SA, cudaStream_t s) {
   if (n <= 0) return JMG_OK;
-  JMG_CUDA(cudaMemsetAsync(rowmax, 0, sizeof(double) * n, s));
   const unsigned tiles = (unsigned)tri_tiles(cdiv(n, 64));
-  k_oz_rowmax<<<tiles, 256, 0, s>>>(n, A, lda, rowmax);
-  JMG_TRY(launched());
   const int lds = (int)round_up((size_t)n, 64);
   k_oz_slice_a<<<tiles, 256, 0, s>>>(n, A, lda, rowmax, (__nv_bfloat16*)SA, lds,
                                      (size_t)lds * n);

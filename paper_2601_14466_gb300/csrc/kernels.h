@@ -92,12 +92,20 @@ size_t oz_a_bytes(int n);             // slices of A
 size_t oz_x_bytes(int n, int nrhs);   // slices of X and their exponents
 int oz_splits(int n, int nrhs);       // K splits requested
 int oz_splits_used(int n, int nrhs);  // K splits the grid ends up with (partials written)
-// rowmax: n doubles; SA: oz_a_bytes(n)
+// rowmax: n doubles (written); SA: oz_a_bytes(n)
 int oz_prepare_a(int n, const double* A, int lda, double* rowmax, void* SA, cudaStream_t s);
+// the slices alone, from row maxima already computed by launch_row_stats
+int oz_slice_a(int n, const double* A, int lda, const double* rowmax, void* SA, cudaStream_t s);
 // part[z] (z < oz_splits_used) = partial sums of A X; xwork: oz_x_bytes(n, nrhs)
 int oz_product(int n, int nrhs, const void* SA, const double* rowmax, const double* X, int ldx,
                void* xwork, double* part, int* err, cudaStream_t s);
 
+// Row sums and row maxima of |A| over full rows of the symmetric A (lower
+// stored); either output may be null.
+int launch_row_stats(int n, const double* A, int lda, double* rowsum, double* rowmax,
+                     cudaStream_t s);
+// *out = max_i v[i] (NaN propagates; v >= 0)
+int launch_max_reduce(int n, const double* v, double* out, cudaStream_t s);
 // ||A||_inf (lower stored) into *out; rowsum: n doubles of scratch.
 int launch_norm_inf(int n, const double* A, int lda, double* rowsum, double* out,
                     cudaStream_t s);
