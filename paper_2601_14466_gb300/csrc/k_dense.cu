@@ -346,71 +346,105 @@ int launch_trsm(double* A21, int lda, int m, int kb, const double* Lkk, const in
                 cudaStream_t s) {
   return trsm_impl<double, 32>(A21, lda, m, kb, Lkk, info, s);
 }
-// FP32 panel TRSM of the mixed path (kb == KB): one thread per row solves
-// x Lkk^T = a in 32-column chunks.  Chunk J starts from a_J, subtracts the
-// finished chunks K < J (x_K L_JK^T, read back from shared memory where this
-// thread parked them) and then solves with the diagonal 32 x 32 block
-// right-looking (x_k = a_k / L_kk, a_c -= x_k L_ck).  Lkk sits in shared memory
-// transposed (Lt[k][c] = L[c][k]) so every warp reads it as broadcasts; only
-// the 32 values of the current chunk live in registers.
+// FP32 panel TRSM of the mixed path (kb == KB): row r of the panel solves
+// x Lkk^T = a by forward substitution, four threads per row (lanes 4r' .. 4r'+3
+// of a warp), each owning 8 of every 32 columns.  Columns go in 32-wide chunks:
+// chunk J first subtracts the finished chunks (x_k L_ck for k < 32J, an
+// independent FMA per column: the bulk of the work, spread over the four
+// threads), then solves its diagonal 32 x 32 block (x_k = a_k / L_kk by the
+// owner, broadcast to the row's other three lanes by a shuffle, a_c -= x_k L_ck).
+// The 64-row tile of the panel and L_kk (transposed, Lt[k][c] = L[c][k]) sit in
+// shared memory; global traffic is coalesced down the columns.
+namespace ptrsm {
+constexpr int RB = 64, TH = 256, LDX = RB + 1;
+}
+
 template <int KB>
-__global__ void __launch_bounds__(128) k_trsm_rows(float* __restrict__ A21, int lda, int m,
-                                                   const float* __restrict__ Lkk,
-                                                   const int* __restrict__ info) {
+__global__ void __launch_bounds__(ptrsm::TH, 1) k_trsm_rows(float* __restrict__ A21, int lda, int m,
+                                                        const float* __restrict__ Lkk,
+                                                        const int* __restrict__ info) {
+  using namespace ptrsm;
   if (*(volatile const int*)info != 0) return;
   extern __shared__ __align__(16) float sm_trows[];
-  float(*Lt)[KB] = reinterpret_cast<float(*)[KB]>(sm_trows);       // KB x KB
-  float(*Xs)[128] = reinterpret_cast<float(*)[128]>(sm_trows + KB * KB);  // (KB-32) x 128
-  float* rinv = sm_trows + KB * KB + (KB - 32) * 128;
+  float(*Lt)[KB] = reinterpret_cast<float(*)[KB]>(sm_trows);            // KB x KB
+  float(*Xt)[LDX] = reinterpret_cast<float(*)[LDX]>(sm_trows + KB * KB);  // KB x RB (column-major tile)
+  float* rinv = sm_trows + KB * KB + KB * LDX;
   const int t = threadIdx.x;
-  for (int base = 0; base < KB * KB; base += 128 * 16) {
+  const int r0 = blockIdx.x * RB;
+  for (int base = 0; base < KB * KB; base += TH * 16) {  // 16 independent loads per thread
     float v[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const int idx = base + t + 128 * q;
+      const int idx = base + t + TH * q;
       const int c = idx % KB, k = idx / KB;  // column k of L, row c
-      v[q] = (c >= k) ? Lkk[(size_t)k * lda + c] : 0.0f;
+      v[q] = (idx < KB * KB && c >= k) ? Lkk[(size_t)k * lda + c] : 0.0f;
     }
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const int idx = base + t + 128 * q;
-      Lt[idx / KB][idx % KB] = v[q];
+      const int idx = base + t + TH * q;
+      if (idx < KB * KB) Lt[idx / KB][idx % KB] = v[q];
+    }
+  }
+  for (int base = 0; base < KB * RB; base += TH * 16) {
+    float v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int idx = base + t + TH * q;
+      const int r = idx % RB, c = idx / RB;
+      v[q] = (idx < KB * RB && r0 + r < m) ? A21[(size_t)c * lda + r0 + r] : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int idx = base + t + TH * q;
+      if (idx < KB * RB) Xt[idx / RB][idx % RB] = v[q];
     }
   }
   __syncthreads();
   if (t < KB) rinv[t] = 1.0f / Lt[t][t];
   __syncthreads();
-  const int r = blockIdx.x * 128 + t;
-  if (r >= m) return;
+  const int rl = t / 4, g = t % 4, lane = t % 32;
+#pragma unroll 1
   for (int J = 0; J < KB / 32; ++J) {
-    const int j0 = J * 32;
-    float x[32];
+    const int j0 = J * 32, cb = j0 + 8 * g;  // this thread's 8 columns
+    float x[8];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) x[c] = A21[(size_t)(j0 + c) * lda + r];
+    for (int i = 0; i < 8; ++i) x[i] = Xt[cb + i][rl];
+    // the finished chunks
+#pragma unroll 4
     for (int k = 0; k < j0; ++k) {
-      const float xk = Xs[k][t];
-      const float4* lrow = reinterpret_cast<const float4*>(&Lt[k][j0]);
+      const float xk = Xt[k][rl];
+      const float4 l0 = *reinterpret_cast<const float4*>(&Lt[k][cb]);
+      const float4 l1 = *reinterpret_cast<const float4*>(&Lt[k][cb + 4]);
+      x[0] = fmaf(-xk, l0.x, x[0]);
+      x[1] = fmaf(-xk, l0.y, x[1]);
+      x[2] = fmaf(-xk, l0.z, x[2]);
+      x[3] = fmaf(-xk, l0.w, x[3]);
+      x[4] = fmaf(-xk, l1.x, x[4]);
+      x[5] = fmaf(-xk, l1.y, x[5]);
+      x[6] = fmaf(-xk, l1.z, x[6]);
+      x[7] = fmaf(-xk, l1.w, x[7]);
+    }
+    // the diagonal block of the chunk
 #pragma unroll
-      for (int c4 = 0; c4 < 8; ++c4) {
-        const float4 l = lrow[c4];
-        x[4 * c4 + 0] -= xk * l.x;
-        x[4 * c4 + 1] -= xk * l.y;
-        x[4 * c4 + 2] -= xk * l.z;
-        x[4 * c4 + 3] -= xk * l.w;
-      }
+    for (int kk = 0; kk < 32; ++kk) {
+      const int k = j0 + kk, go = kk / 8, io = kk % 8;
+      if (g == go) x[io] *= rinv[k];
+      const float xk = __shfl_sync(0xffffffffu, x[io], (lane & ~3) | go);
+      const float4 l0 = *reinterpret_cast<const float4*>(&Lt[k][cb]);
+      const float4 l1 = *reinterpret_cast<const float4*>(&Lt[k][cb + 4]);
+      const float l[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (8 * g + i > kk) x[i] = fmaf(-xk, l[i], x[i]);
     }
 #pragma unroll
-    for (int k = 0; k < 32; ++k) {
-      x[k] *= rinv[j0 + k];
-#pragma unroll
-      for (int c = k + 1; c < 32; ++c) x[c] -= x[k] * Lt[j0 + k][j0 + c];
-    }
-    if (J < KB / 32 - 1) {
-#pragma unroll
-      for (int c = 0; c < 32; ++c) Xs[j0 + c][t] = x[c];
-    }
-#pragma unroll
-    for (int c = 0; c < 32; ++c) A21[(size_t)(j0 + c) * lda + r] = x[c];
+    for (int i = 0; i < 8; ++i) Xt[cb + i][rl] = x[i];
+    __syncwarp();  // the row's four lanes read these in the next chunks
+  }
+  __syncthreads();
+  for (int idx = t; idx < KB * RB; idx += TH) {
+    const int r = idx % RB, c = idx / RB;
+    if (r0 + r < m) A21[(size_t)c * lda + r0 + r] = Xt[c][r];
   }
 }
 
@@ -419,9 +453,9 @@ int launch_trsm(float* A21, int lda, int m, int kb, const float* Lkk, const int*
   if (m <= 0) return JMG_OK;
   if (kb == 128 || kb == 64) {
     auto k = (kb == 128) ? k_trsm_rows<128> : k_trsm_rows<64>;
-    const size_t smem = sizeof(float) * ((size_t)kb * kb + (size_t)(kb - 32) * 128 + kb);
+    const size_t smem = sizeof(float) * ((size_t)kb * kb + (size_t)kb * ptrsm::LDX + kb);
     JMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k<<<cdiv(m, 128), 128, smem, s>>>(A21, lda, m, Lkk, info);
+    k<<<cdiv(m, ptrsm::RB), ptrsm::TH, smem, s>>>(A21, lda, m, Lkk, info);
     return launched();
   }
   return trsm_impl<float, 64>(A21, lda, m, kb, Lkk, info, s);
