@@ -138,12 +138,12 @@ int jmg_potrs(int n, int nrhs, const void* L, int lda, void* B, int ldb, int dty
  * handed out at start-up, a host framework that owns every device byte through
  * its own pool, or plain C callers without a device allocator -- and so cannot
  * pass the scratch that jmg_potrs wants.  It allocates nothing (no cudaMalloc,
- * no cudaFree, no allocating library routine); its scratch is a fixed 16 KiB
+ * no cudaFree, no allocating library routine); its scratch is a fixed 256 KiB
  * array in device memory that every GPU loading the library keeps until the
  * process exits.
  *   Arguments and results as jmg_potrs (FP64 only).
- *   Limit: 2 * ceil(nrhs/16) + 1 <= 4096 ints of scratch
- *     (nrhs <= 32752, any n); larger problems return JMG_ERR_WORKSPACE
+ *   Limit: ceil(nrhs/16) * (2 + ceil(n/32)) + 1 <= 65536 ints of
+ *     scratch (e.g. nrhs <= 496 at n = 65536); larger problems return JMG_ERR_WORKSPACE
  *     with nothing queued.
  *   The first call on a device, with that device current, looks up the device
  *     address of the array (cudaGetSymbolAddress); make that first call before

@@ -57,6 +57,15 @@ JMG_DEV uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// Volatile read of a flag in shared memory.  (A volatile access through a
+// generic pointer is ordered behind the thread's outstanding global loads and
+// stores, so a flag check written that way waits for them.)
+JMG_DEV int ld_shared_volatile(const int* p) {
+  int v;
+  asm volatile("ld.volatile.shared.b32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+  return v;
+}
+
 JMG_DEV uint64_t globaltimer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

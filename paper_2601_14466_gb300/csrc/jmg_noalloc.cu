@@ -1,8 +1,8 @@
 // jmg_noalloc.cu -- jmg_potrs_static: the FP64 solve with a Cholesky factor
 // that needs no scratch from the caller and allocates nothing.
 //
-// jmg_potrs takes its scratch (the tickets, counters and error word of
-// the one-launch triangular solves) from a caller-provided `work` buffer.  Some
+// jmg_potrs takes its scratch (the tickets, counters, flags and error
+// word of the one-launch triangular solves) from a caller-provided `work` buffer.  Some
 // callers cannot provide one: code that runs after device memory has been
 // handed out once and for all (a fixed memory budget set at start-up, or a
 // host framework that owns every device byte through its own pool), and plain
@@ -17,11 +17,11 @@
 namespace jmg {
 namespace {
 
-// Fixed scratch: 4096 ints (16 KiB), resident on every GPU that loads the
+// Fixed scratch: 65536 ints (256 KiB), resident on every GPU that loads the
 // library until the process exits.  Every call shares it and it keeps the last
 // call's contents; the solve launcher clears the part it uses before each
 // launch.
-constexpr int kStaticScratchInts = 4096;
+constexpr int kStaticScratchInts = 65536;
 static __device__ __align__(256) int g_solve_scratch[kStaticScratchInts];
 
 // Host-side device address of g_solve_scratch, one per device, looked up on the

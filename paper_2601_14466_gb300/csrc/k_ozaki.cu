@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
           atomicExch(&s_fail, 1);
           break;
         }
-        if (*(volatile int*)&s_fail) break;
+        if (ld_shared_volatile(&s_fail)) break;
         mbar_expect_tx(&xfull[xs], S * X_TILE);
         for (int b = 0; b < S; ++b)
           tma_load_2d(xbuf + xs * X_BUF + b * X_TILE, &tmX, kb * BK, b * nrhs_pad + ct * N,
@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
       for (int c = 0; c < CW; ++c) hs[c] = ls[c] = 0ull;
       bool ok = true;
       for (int w = w0; w < w1; ++w) {
-        if (!mbar_wait(accf, (uint32_t)((w - w0) & 1)) || *(volatile int*)&s_fail) {
+        if (!mbar_wait(accf, (uint32_t)((w - w0) & 1)) || ld_shared_volatile(&s_fail)) {
           ok = false;
           break;
         }
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
   }
   __syncwarp();
   __syncthreads();
-  if (*(volatile int*)&s_fail) {
+  if (ld_shared_volatile(&s_fail)) {
     if (warp == 0 && lane == 0) {
       for (long long u = (x_issued > 2 ? x_issued - 2 : 0); u < x_issued; ++u)
         (void)mbar_wait(&xfull[u & 1], (uint32_t)(u >> 1) & 1);

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(PTHREADS, 1)
             atomicExch(&s_fail, 1);
             break;
           }
-          if (*(volatile int*)&s_fail) break;
+          if (ld_shared_volatile(&s_fail)) break;
           unsigned char* sa = smem + s * STAGE_BYTES;
           mbar_expect_tx(&full[s], STAGE_BYTES);
           const int kx = kb * (KIND == 0 ? BK : 2 * BK);  // element coordinate of the stage
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(PTHREADS, 1)
           tma_load_2d(sa + TILE_BYTES, &tmB, kx, tj * BN, &full[s]);
           ++issued;
         }
-        if (*(volatile int*)&s_fail) break;
+        if (ld_shared_volatile(&s_fail)) break;
       }
     }
   } else if (warp == 1) {
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(PTHREADS, 1)
       const int a = i & 1;
       const bool ok = mbar_wait(&acc_full[a], (uint32_t)(i / 2) & 1);
       tc_fence_after();
-      if (!ok || *(volatile int*)&s_fail) {
+      if (!ok || ld_shared_volatile(&s_fail)) {
         atomicExch(&s_fail, 1);
         break;
       }
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(PTHREADS, 1)
 
   // ---- teardown
   __syncthreads();
-  if (*(volatile int*)&s_fail) {
+  if (ld_shared_volatile(&s_fail)) {
     if (warp == 0 && lane == 0) {
       // let every copy this CTA issued land before the CTA exits
       for (long long g = (issued > PSTAGES ? issued - PSTAGES : 0); g < issued; ++g)

@@ -45,7 +45,7 @@ int launch_trsv_diag(int kb, int nrhs, const T* L, int lda, T* B, int ldb, int t
 
 // One-launch blocked solve with the whole factor, in place on B:
 // trans == 0: L Y = B;  trans == 1: L^T X = B.  `sync` holds
-// trsv_sync_ints(n, nrhs) ints of scratch (tickets, finished-block counters, error word).
+// trsv_sync_ints(n, nrhs) ints of scratch (tickets, finished-block counters, per-block flags, error word).
 size_t trsv_sync_ints(int n, int nrhs);
 template <typename T>
 int launch_trsv_persist(int n, int nrhs, const T* L, int lda, T* B, int ldb, int trans, int* sync,

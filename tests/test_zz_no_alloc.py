@@ -52,7 +52,7 @@ def test_potrs_static_matches_potrs_twice(n, nrhs):
 
 
 def test_potrs_static_rejects_oversize():
-    # 4096 ints of scratch: nrhs = 32768 needs 2 * 2048 + 1 > 4096
+    # 65536 ints of scratch: nrhs = 512 at n = 65536 needs 32 * (2 + 2048) + 1 > 65536
     lib = jmg.load()
-    rc = lib.jmg_potrs_static(65536, 32768, 256, 65536, 512, 65536, jmg.JMG_F64, None)
+    rc = lib.jmg_potrs_static(65536, 512, 256, 65536, 512, 65536, jmg.JMG_F64, None)
     assert rc == 2  # JMG_ERR_WORKSPACE, nothing queued
