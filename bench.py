@@ -49,6 +49,14 @@ WORKLOADS = {
 
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 
+# DRAM bytes (read + write) of one k_trsv_persist<float> launch, from one ncu
+# capture (profiles/k_trsv_persist_n16384_nrhs64.md); None where not captured.
+_SOLVE_TRAFFIC = {}
+
+
+def SOLVE_TRAFFIC_BYTES(n, nrhs):
+    return _SOLVE_TRAFFIC.get((n, nrhs))
+
 
 def nominal_flops(n, nrhs):
     return n ** 3 / 3.0 + 2.0 * n * n * nrhs
@@ -288,14 +296,62 @@ def run_ours(args, w, rank, world):
     t_e2e = te if e2e_steps > 0 else None
 
     value = world * F * args.steps / t_mixed / 1e12
-    # roofline of the dominant kernel: the FP64 A*X GEMM of the residual / PCG
-    # (2 n^2 nrhs flops per launch), timed by the library with CUDA events
+    # Rooflines, from the library's CUDA events inside the timed steps (timing=True
+    # records events around the solves, the residual products and the factor only).
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
+    peak_src = "of measured (MEASURED_PEAKS.json)" if peaks else "of fallback"
+    n_sol = sum(si.n_solve for si in infos)
+    t_sol = sum(si.t_solve_gpu_ms for si in infos)
     n_res = sum(si.n_resid for si in infos)
     t_res = sum(si.t_resid_gpu_ms for si in infos)
-    achieved = 2.0 * n * n * nrhs / (t_res / max(n_res, 1) / 1e3) / 1e12 if n_res else None
-    probe_f, probe_ms = jmg.probe(0, 608, 3000, dev)
-    probe_tf = probe_f / probe_ms / 1e9
-    share = t_res / 1e3 / (t_mixed / world) if n_res else None
+    t_fac = sum(si.t_factor_gpu_ms for si in infos)
+    steps_ms = t_mixed * 1e3 / world
+    # dominant kernel: the one-launch triangular solve with the FP32 factor
+    # (k_trsv_persist, two launches per solve).  Algorithmic bytes per launch:
+    # the lower triangle of L once (FP32) and one read + write of the n x nrhs block.
+    sol_bytes = n * (n + 1) / 2 * 4 + 2 * n * nrhs * 4
+    sol_launch_ms = t_sol / (2 * n_sol) if n_sol else None
+    sol_gbs = sol_bytes / (sol_launch_ms / 1e3) / 1e9 if n_sol else None
+    roof = {"kernel": "k_trsv_persist<float> (forward / backward solve with the FP32 factor)",
+            "bound": "hbm", "achieved": round(sol_gbs, 2) if sol_gbs else None,
+            "peak": hbm, "unit": "GB/s",
+            "frac": round(sol_gbs / hbm, 4) if sol_gbs else None, "peak_source": peak_src,
+            "traffic": SOLVE_TRAFFIC_BYTES(n, nrhs),
+            "algorithmic_bytes_per_launch": sol_bytes,
+            "launch_ms": round(sol_launch_ms, 4) if sol_launch_ms else None,
+            "launches": 2 * n_sol,
+            "share_of_step": round(t_sol / steps_ms, 4) if n_sol else None,
+            "note": "latency-bound serial chain of n/32 blocks; see profiles/"}
+    # the split FP64-accurate residual product on the BF16 tensor cores
+    # (k_oz_gemm): 36 slice pairs x 2 n^2 nrhs BF16 MMA flops per product
+    res_launch_ms = t_res / n_res if n_res else None
+    kern = {}
+    if n_res:
+        mma = 36 * 2.0 * n * n * nrhs if args.resid != "fp64" else None
+        kern["residual_product"] = {
+            "kernel": "k_oz_gemm (split, BF16 tensor cores)" if mma else "k_gemm<double> (FP64)",
+            "bound": "tensor" if mma else "alu",
+            "achieved": round((mma if mma else 2.0 * n * n * nrhs) / (res_launch_ms / 1e3) / 1e12, 3),
+            "peak": bf16 if mma else FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+            "fp64_equivalent_tflops": round(2.0 * n * n * nrhs / (res_launch_ms / 1e3) / 1e12, 3),
+            "launch_ms": round(res_launch_ms, 4), "launches": n_res,
+            "share_of_step": round(t_res / steps_ms, 4)}
+        kern["residual_product"]["frac"] = round(kern["residual_product"]["achieved"] /
+                                                 kern["residual_product"]["peak"], 4)
+    if t_fac > 0:
+        pairs = {1: 1, 2: 3, 3: 6}.get(words, 1) if prec != "fp8" else 1
+        mma_f = pairs * n ** 3 / 3.0
+        pk = bf16 * (2.0 if prec == "fp8" else 1.0)  # e4m3: twice the 16-bit rate (nominal ratio)
+        kern["factor"] = {"kernels": "k_potrf_diag + k_trsm_rows + k_split_words/k_quant_fp8 + "
+                                     "k_syrk_tc (tensor-core update)",
+                          "bound": "tensor", "unit": "TFLOP/s",
+                          "achieved": round(mma_f / (t_fac / len(infos) / 1e3) / 1e12, 3),
+                          "peak": pk, "ms": round(t_fac / len(infos), 3),
+                          "note": "tensor-core MMA flops of the trailing updates (%d word pairs) "
+                                  "over the whole factorisation time" % pairs}
+        kern["factor"]["frac"] = round(kern["factor"]["achieved"] / pk, 4)
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -315,15 +371,8 @@ def run_ours(args, w, rank, world):
         "phases_ms": {"factor": round(statistics.mean(si.t_factor_ms for si in infos), 3),
                       "solve": round(statistics.mean(si.t_solve_ms for si in infos), 3),
                       "refine": round(statistics.mean(si.t_refine_ms for si in infos), 3)},
-        "roofline": {"kernel": "k_gemm<double,*,S,N,PART> (FP64 A*X of residual / PCG)",
-                     "bound": "alu", "achieved": round(achieved, 4) if achieved else None,
-                     "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                     "frac": round(achieved / FP64_NOMINAL_TFLOPS, 4) if achieved else None,
-                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25)",
-                     "peak_probe_dfma": round(probe_tf, 4),
-                     "frac_of_probe": round(achieved / probe_tf, 4) if achieved else None,
-                     "share_of_step": round(share, 4) if share else None,
-                     "launches": n_res, "traffic": None},
+        "roofline": roof,
+        "kernels": kern,
         "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
         "clocks": clocks,
     }

@@ -97,6 +97,9 @@ typedef struct {
   int n_resid;           /* number of FP64 A*X evaluations (residuals and PCG products)  */
   int n_hist;            /* entries of eta_hist written (may exceed 32: first 32 kept)   */
   double eta_hist[32];   /* max_j backward error after each residual / PCG step          */
+  double t_solve_gpu_ms; /* with opt->timing: summed CUDA-event time of the triangular   */
+  int n_solve;           /*   solve pairs (L Y = R, L^T Z = Y) and their number          */
+  double t_factor_gpu_ms; /* with opt->timing: CUDA-event time of the factorisations    */
 } jmg_stats;
 
 /* Fill *opt with the defaults: nb 128, NB 128, prec NATIVE, words 1, tol 1e-13,

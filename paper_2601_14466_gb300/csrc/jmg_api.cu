@@ -180,9 +180,11 @@ static int sync_read(void* host, const void* dev, size_t bytes, cudaStream_t s) 
 // `status` is a device int set to -1 if a device-side wait of the solve ran out.
 static int precond_update(int n, int nrhs, const float* W, int ldw, const double* R,
                           const double* colmax_r, float* D, double* X, int* sync, int* status,
-                          cudaStream_t s) {
+                          cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
   JMG_TRY(launch_scale_to_f32(n, nrhs, R, n, colmax_r, D, n, s));
+  if (e0) JMG_CUDA(cudaEventRecord(e0, s));
   JMG_TRY(solve_llt<float>(n, nrhs, W, ldw, D, n, sync, status, s));
+  if (e1) JMG_CUDA(cudaEventRecord(e1, s));
   JMG_TRY(launch_axpy_f32(n, nrhs, D, n, colmax_r, X, n, s));
   return JMG_OK;
 }
@@ -201,7 +203,8 @@ struct MixedCtx {
   float* D;
   int* ints;  // [0] factor info, [1] factor err, [2] solve status, [3] PCG breakdown
   int* sync;
-  cudaEvent_t ev[2];
+  cudaEvent_t ev[6];  // timing: [0,1] residual product, [2,3] solve, [4,5] factor
+  bool solve_pending = false;
   jmg_stats* S;
   std::vector<double> eh;
 };
@@ -227,6 +230,17 @@ static int product(MixedCtx& c, const double* Xin, const double* Bin, int ldbin,
                              ldbin, Rout, c.n, c.colmax, c.s);
 }
 
+// after a stream synchronisation: add the timed solve (if one is pending)
+static int collect_solve(MixedCtx& c) {
+  if (!c.solve_pending) return JMG_OK;
+  float ms = 0.f;
+  JMG_CUDA(cudaEventElapsedTime(&ms, c.ev[2], c.ev[3]));
+  c.S->t_solve_gpu_ms += ms;
+  c.S->n_solve++;
+  c.solve_pending = false;
+  return JMG_OK;
+}
+
 // R = B - A X (true residual), eta -> host; returns max eta in c.eh[0]
 static int true_residual(MixedCtx& c) {
   JMG_TRY(product(c, c.X, c.B, c.ldb, c.R));
@@ -237,6 +251,7 @@ static int true_residual(MixedCtx& c) {
     float ms = 0.f;
     JMG_CUDA(cudaEventElapsedTime(&ms, c.ev[0], c.ev[1]));
     c.S->t_resid_gpu_ms += ms;
+    JMG_TRY(collect_solve(c));
   }
   return JMG_OK;
 }
@@ -244,7 +259,12 @@ static int true_residual(MixedCtx& c) {
 // Z = M^{-1} R with the FP32 factor (per-column scaling by ||r_c||)
 static int precond_to(MixedCtx& c, double* Zout) {
   JMG_TRY(launch_scale_to_f32(c.n, c.nrhs, c.R, c.n, c.colmax, c.D, c.n, c.s));
+  if (c.ev[2]) JMG_CUDA(cudaEventRecord(c.ev[2], c.s));
   JMG_TRY(solve_llt<float>(c.n, c.nrhs, c.W, c.p->ldw, c.D, c.n, c.sync, &c.ints[2], c.s));
+  if (c.ev[3]) {
+    JMG_CUDA(cudaEventRecord(c.ev[3], c.s));
+    c.solve_pending = true;
+  }
   return launch_scale_from_f32(c.n, c.nrhs, c.D, c.colmax, Zout, c.s);
 }
 
@@ -272,6 +292,7 @@ static int pcg(MixedCtx& c, bool* breakdown) {
       float ms = 0.f;
       JMG_CUDA(cudaEventElapsedTime(&ms, c.ev[0], c.ev[1]));
       c.S->t_resid_gpu_ms += ms;
+      JMG_TRY(collect_solve(c));
     }
     c.S->n_resid++;
     c.S->iters++;
@@ -313,7 +334,7 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
   c.pq = c.rz + 2 * nrhs;
   c.ints = at<int>(work, p.off_ints);
   c.sync = at<int>(work, p.off_sync);
-  c.ev[0] = c.ev[1] = nullptr;
+  for (auto& e : c.ev) e = nullptr;
   c.S = st ? st : &local;
   c.eh.assign(1 + nrhs, 0.0);
   jmg_stats& S = *c.S;
@@ -321,14 +342,13 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
   S.words_used = o.words;
   S.refine_used = JMG_REFINE_IR;
   if (o.timing) {
-    JMG_CUDA(cudaEventCreate(&c.ev[0]));
-    JMG_CUDA(cudaEventCreate(&c.ev[1]));
+    for (auto& e : c.ev) JMG_CUDA(cudaEventCreate(&e));
   }
   struct EvGuard {
     cudaEvent_t* e;
     ~EvGuard() {
-      if (e[0]) cudaEventDestroy(e[0]);
-      if (e[1]) cudaEventDestroy(e[1]);
+      for (int i = 0; i < 6; ++i)
+        if (e[i]) cudaEventDestroy(e[i]);
     }
   } guard{c.ev};
 
@@ -364,10 +384,17 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
     if (!o.reuse_factor || attempt > 0) {
       for (;;) {  // factor, shifting the diagonal while the low-precision factor breaks down
         JMG_CUDA(cudaMemsetAsync(c.ints, 0, sizeof(int) * 4, s));
+        if (c.ev[4]) JMG_CUDA(cudaEventRecord(c.ev[4], s));
         JMG_TRY(launch_lower_to_f32(n, A, lda, c.W, p.ldw, shift, s));
         JMG_TRY(factor_mixed(n, c.W, p.ldw, o, p, work, &c.ints[0], &c.ints[1], s));
+        if (c.ev[5]) JMG_CUDA(cudaEventRecord(c.ev[5], s));
         int hs[2] = {0, 0};
         JMG_TRY(sync_read(hs, c.ints, sizeof(hs), s));
+        if (c.ev[5]) {
+          float ms = 0.f;
+          JMG_CUDA(cudaEventElapsedTime(&ms, c.ev[4], c.ev[5]));
+          S.t_factor_gpu_ms += ms;
+        }
         S.factor_tries++;
         if (hs[1]) return S.status = JMG_ERR_TIMEOUT;
         if (hs[0] == 0) break;
@@ -395,7 +422,9 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
       k_copy_colmax<<<grid, 256, 0, s>>>(n, B, ldb, c.R, c.colmax);
       JMG_TRY(launched());
     }
-    JMG_TRY(precond_update(n, nrhs, c.W, p.ldw, c.R, c.colmax, c.D, c.X, c.sync, &c.ints[2], s));
+    JMG_TRY(precond_update(n, nrhs, c.W, p.ldw, c.R, c.colmax, c.D, c.X, c.sync, &c.ints[2], s,
+                           c.ev[2], c.ev[3]));
+    c.solve_pending = c.ev[3] != nullptr;
     const double t2 = now_ms();
     S.t_solve_ms += t2 - t1;
 
@@ -425,7 +454,8 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
       prev = c.eh[0];
       if (!use_pcg) {
         JMG_TRY(precond_update(n, nrhs, c.W, p.ldw, c.R, c.colmax, c.D, c.X, c.sync, &c.ints[2],
-                               s));
+                               s, c.ev[2], c.ev[3]));
+        c.solve_pending = c.ev[3] != nullptr;
         S.iters++;
         continue;
       }

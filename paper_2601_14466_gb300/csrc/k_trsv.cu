@@ -38,32 +38,37 @@ constexpr int KCH = 2;    // finished blocks a helper multiplies per step (at mo
 constexpr int RING = 4;   // helper: blocks of L in flight or in use (KCH + 2)
 constexpr uint64_t WAIT_NS = 2000000000ull;
 
-// right-hand sides per group (all of them, up to 64, for FP32; 16 for FP64) and
-// the register tile of the products: TM rows x TN columns per thread
+// right-hand sides per group (all of them, up to 64, for FP32; 16 for FP64),
+// the register tile of the products (TM rows x TN columns per thread), and the
+// row padding of the blocks of L (rows stay 16-byte aligned for the vector
+// loads).  Row-of-Y buffers are padded by one element (a row stride of
+// 1 mod 32 words keeps column-wise accesses free of bank conflicts).
 template <typename T>
 struct Cfg;
 template <>
 struct Cfg<float> {
-  static constexpr int NR = 64, TM = 2, TN = 4, PAD = 4;
+  static constexpr int NR = 64, TM = 2, TN = 4, PADL = 4;
 };
 template <>
 struct Cfg<double> {
-  static constexpr int NR = 16, TM = 2, TN = 1, PAD = 2;
+  static constexpr int NR = 16, TM = 2, TN = 1, PADL = 2;
 };
+
+constexpr int PADY = 1;
 
 template <typename T>
 struct Helper {
-  static constexpr int NR = Cfg<T>::NR, PAD = Cfg<T>::PAD;
-  T Ls[RING][NBK][NBK + PAD];  // blocks of L: Ls[slot][k][i] = factor entry (row i, col k)
-  T Ys[KCH][NBK][NR + PAD];    // finished rows of Y
+  static constexpr int NR = Cfg<T>::NR, PADL = Cfg<T>::PADL;
+  T Ls[RING][NBK][NBK + PADL];  // blocks of L: Ls[slot][k][i] = factor entry (row i, col k)
+  T Ys[KCH][NBK][NR + PADY];    // finished rows of Y
 };
 template <typename T>
 struct Leader {
-  static constexpr int NR = Cfg<T>::NR, PAD = Cfg<T>::PAD;
-  static constexpr int PB = (NBK * (NR + PAD) + NR - 1) / NR;  // >= NBK: also holds Ss
-  T Lo[2][LAG - 1][NBK][NBK + PAD];  // off-diagonal blocks of the next two steps, [k][i]
+  static constexpr int NR = Cfg<T>::NR, PADL = Cfg<T>::PADL;
+  static constexpr int PB = (NBK * (NR + PADY) + NR - 1) / NR;  // >= NBK: also holds Ss
+  T Lo[2][LAG - 1][NBK][NBK + PADL];  // off-diagonal blocks of the next two steps, [k][i]
   T Ld[2][NBK][NBK + 1];             // diagonal blocks: Ld[r][c] = L(r0 + r, r0 + c)
-  T Yr[LAG - 1][NBK][NR + PAD];      // the last LAG-1 solved blocks (ring)
+  T Yr[LAG - 1][NBK][NR + PADY];      // the last LAG-1 solved blocks (ring)
   T Pb[2][NR][PB];                   // P_d column-major (Pb[c][r]); then reused as Ss[r][c]
   T rinv[2][NBK];
 };
@@ -189,7 +194,8 @@ JMG_DEV void block_product(const T (*Lq)[LDL], const T (*Yq)[LDY], int ti, int t
   for (int kk = 0; kk < NBK; ++kk) {
     T a[TM], y[TN];
     Vec<T, TM>::load(&Lq[kk][ti], a);
-    Vec<T, TN>::load(&Yq[kk][tj], y);
+#pragma unroll
+    for (int j = 0; j < TN; ++j) y[j] = Yq[kk][tj + j];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -204,7 +210,7 @@ __global__ void __launch_bounds__(trsv::TH, 2)
                    int trans, int g0, int* __restrict__ tickets, int* __restrict__ done,
                    int* __restrict__ pflag, int* __restrict__ err, int* __restrict__ info) {
   using namespace trsv;
-  constexpr int NR = Cfg<T>::NR, TM = Cfg<T>::TM, TN = Cfg<T>::TN, PAD = Cfg<T>::PAD;
+  constexpr int NR = Cfg<T>::NR, TM = Cfg<T>::TM, TN = Cfg<T>::TN, PADL = Cfg<T>::PADL;
   constexpr int RG = NBK / TM;  // row groups; column groups = TH / RG
   static_assert(RG * (NR / TN) == CT, "thread tile does not cover the block");
   if (info && *(volatile int*)info != 0) return;  // no factor: leave B alone
@@ -301,7 +307,7 @@ __global__ void __launch_bounds__(trsv::TH, 2)
         }
         for (int e = 1; e < LAG; ++e) {
           if (d - e < 0) continue;
-          copy_offdiag<T, NBK + PAD, CT>(M.Lo[buf][e - 1], L, lda, n, r0, rows, blk(d - e), trans, t);
+          copy_offdiag<T, NBK + PADL, CT>(M.Lo[buf][e - 1], L, lda, n, r0, rows, blk(d - e), trans, t);
         }
         cp_async_commit();
       };
@@ -326,10 +332,10 @@ __global__ void __launch_bounds__(trsv::TH, 2)
         if (t < NBK) M.rinv[buf][t] = (t < rows) ? T(1) / M.Ld[buf][t][t] : T(0);
         for (int e = 1; e < LAG; ++e)
           if (d - e >= 0)
-            block_product<T, NBK + PAD, NR + PAD>(M.Lo[buf][e - 1], M.Yr[(d - e) % (LAG - 1)], ti,
+            block_product<T, NBK + PADL, NR + PADY>(M.Lo[buf][e - 1], M.Yr[(d - e) % (LAG - 1)], ti,
                                                   tj, acc);
         // (every thread read its P_d tile before the barrier above: Ss may overwrite it)
-        T(*Ss)[NR + PAD] = reinterpret_cast<T(*)[NR + PAD]>(&M.Pb[buf][0][0]);
+        T(*Ss)[NR + PADY] = reinterpret_cast<T(*)[NR + PADY]>(&M.Pb[buf][0][0]);
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -359,14 +365,14 @@ __global__ void __launch_bounds__(trsv::TH, 2)
               for (int k = 0; k < i; ++k) s[k] -= Ld[i][k] * x;
             }
           }
-          T(*Y)[NR + PAD] = M.Yr[d % (LAG - 1)];
+          T(*Y)[NR + PADY] = M.Yr[d % (LAG - 1)];
 #pragma unroll
           for (int r = 0; r < NBK; ++r) Y[r][c] = s[r];
         }
         bar_sync(5, CT);
         {
           const int r0 = b * NBK;
-          const T(*Y)[NR + PAD] = M.Yr[d % (LAG - 1)];
+          const T(*Y)[NR + PADY] = M.Yr[d % (LAG - 1)];
           for (int idx = t; idx < NBK * NR; idx += CT) {  // coalesced down the columns
             const int r = idx % NBK, c = idx / NBK;
             if (r < rows && c < ncol) B[(size_t)(c0 + c) * ldb + r0 + r] = Y[r][c];
@@ -387,7 +393,7 @@ __global__ void __launch_bounds__(trsv::TH, 2)
     const int b = blk(d), r0 = b * NBK, rows = min(NBK, n - r0);
     const int ndep = d - LAG + 1;  // dependencies j = 0 .. d-LAG
     auto issue_L = [&](int j) {
-      copy_offdiag<T, NBK + PAD, TH>(H.Ls[j % RING], L, lda, n, r0, rows, blk(j), trans, t);
+      copy_offdiag<T, NBK + PADL, TH>(H.Ls[j % RING], L, lda, n, r0, rows, blk(j), trans, t);
       cp_async_commit();
     };
     T acc[TM][TN];
@@ -431,7 +437,7 @@ __global__ void __launch_bounds__(trsv::TH, 2)
       __syncthreads();
       if (t < CT)
         for (int q = 0; q < ready - j; ++q)
-          block_product<T, NBK + PAD, NR + PAD>(H.Ls[(j + q) % RING], H.Ys[q], ti, tj, acc);
+          block_product<T, NBK + PADL, NR + PADY>(H.Ls[(j + q) % RING], H.Ys[q], ti, tj, acc);
       __syncthreads();  // the ring slots and Ys are free again
       j = ready;
     }

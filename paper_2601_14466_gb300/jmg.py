@@ -58,7 +58,8 @@ class Stats(ctypes.Structure):
                 ("t_factor_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
                 ("t_refine_ms", ctypes.c_double), ("t_resid_gpu_ms", ctypes.c_double),
                 ("n_resid", ctypes.c_int), ("n_hist", ctypes.c_int),
-                ("eta_hist", ctypes.c_double * 32)]
+                ("eta_hist", ctypes.c_double * 32), ("t_solve_gpu_ms", ctypes.c_double),
+                ("n_solve", ctypes.c_int), ("t_factor_gpu_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -224,6 +225,9 @@ class SolveInfo:
     t_resid_gpu_ms: float = 0.0
     n_resid: int = 0
     eta_hist: tuple = ()
+    t_solve_gpu_ms: float = 0.0
+    n_solve: int = 0
+    t_factor_gpu_ms: float = 0.0
 
 
 def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1, nb: int = 128,
@@ -268,7 +272,8 @@ def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1
                        stats.words_used, stats.factor_tries, stats.anorm, stats.t_factor_ms,
                        stats.t_solve_ms, stats.t_refine_ms, stats.refine_used,
                        stats.t_resid_gpu_ms, stats.n_resid,
-                       tuple(stats.eta_hist[i] for i in range(min(stats.n_hist, 32))))
+                       tuple(stats.eta_hist[i] for i in range(min(stats.n_hist, 32))),
+                       stats.t_solve_gpu_ms, stats.n_solve, stats.t_factor_gpu_ms)
         if check and st != 0:
             raise JmgError(st, "jmg_posv")
     return (X[:, 0] if squeeze else X), si

@@ -88,3 +88,22 @@ def test_no_cpu_fallback():
     A = torch.eye(4, dtype=torch.float64)
     with pytest.raises(ValueError):
         jmg.posv(A, torch.ones(4, 1, dtype=torch.float64))
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # the ctypes mirrors of jmg_options / jmg_stats must have the C layout
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "jmg.h"\n'
+                   'int main(void) { printf("%zu %zu %zu %zu %zu\\n", sizeof(jmg_options), '
+                   'sizeof(jmg_stats), offsetof(jmg_stats, eta_hist), '
+                   'offsetof(jmg_stats, n_solve), offsetof(jmg_stats, t_factor_gpu_ms)); '
+                   'return 0; }\n')
+    exe = tmp_path / "sizes"
+    import subprocess
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    want = [ctypes.sizeof(jmg.Options), ctypes.sizeof(jmg.Stats), jmg.Stats.eta_hist.offset,
+            jmg.Stats.n_solve.offset, jmg.Stats.t_factor_gpu_ms.offset]
+    assert got == want
