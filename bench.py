@@ -42,6 +42,8 @@ WORKLOADS = {
                desc="posv n=32768 nrhs=16, A = Q diag(logspace[1,kappa]) Q^T"),
     "c4": dict(n=65536, nrhs=32, kind="gram32", param=1e-2, prec="fp8", words=1,
                desc="posv n=65536 nrhs=32, A = M M^T/n + 1e-2 I (product formed in FP32)"),
+    "c6": dict(n=16384, nrhs=1, kind="diag", param=0.0, prec="bf16", words=1,
+               desc="posv n=16384 nrhs=1, the paper's A = diag(1..N), b = ones (x_i = 1/i)"),
     "c5": dict(n=8192, nrhs=16, kind="gram", param=1.0, prec="bf16", words=2,
                desc="autograd forward+backward n=8192 nrhs=16, A = M M^T/n + I, B ~ N(0,1), "
                     "loss 0.5||X||^2", rhs="normal"),
@@ -133,6 +135,11 @@ def make_inputs(w, device, seed=0):
     from paper_2601_14466_gb300 import inputs
 
     n, nrhs = w["n"], w["nrhs"]
+    if w["kind"] == "diag":  # the paper's matrix: A = diag(1..N), b = ones, x_i = 1/i
+        A, B = inputs.diag_workload(n, device=device)
+        Xt = (1.0 / torch.arange(1, n + 1, dtype=torch.float64, device=device)).reshape(n, 1)
+        torch.cuda.synchronize()
+        return A, Xt, B
     if w["kind"] == "qlam":
         A = inputs.q_lambda(n, w["param"], seed=seed, device=device)
     else:
@@ -159,12 +166,15 @@ def cpu_oracle_sample(w, target_s=12.0):
 
     n_s = min(w["n"], 3072)
     nrhs = w["nrhs"]
-    if w["kind"] == "qlam":
-        A = inputs.q_lambda(n_s, w["param"], seed=11).numpy()
+    if w["kind"] == "diag":
+        A, B = (np.asfortranarray(t.numpy()) for t in inputs.diag_workload(n_s))
     else:
-        A = inputs.gram_shift(n_s, w["param"], seed=11).numpy()  # same construction, FP64
-    X = inputs.uniform(n_s, nrhs, seed=12).numpy()
-    B = np.asfortranarray(A @ X)
+        if w["kind"] == "qlam":
+            A = inputs.q_lambda(n_s, w["param"], seed=11).numpy()
+        else:
+            A = inputs.gram_shift(n_s, w["param"], seed=11).numpy()  # same construction, FP64
+        X = inputs.uniform(n_s, nrhs, seed=12).numpy()
+        B = np.asfortranarray(A @ X)
     oracle.build()
     reps, t_tot = 0, 0.0
     while True:

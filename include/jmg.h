@@ -114,7 +114,9 @@ size_t jmg_workspace_size(int op, int n, int nrhs, int dtype, const jmg_options*
  * the factorisation step of potrs).
  *   n       order of A (n >= 0; n == 0 is a no-op)
  *   A       device, lower(A) in, lower(L) out; lda >= max(1, n)
- *   dtype   JMG_F64 (JMG_F32 returns JMG_ERR_UNSUPPORTED)
+ *   dtype   JMG_F64, or JMG_F32 (FP32 storage: FP32 panel solves and trailing
+ *           updates on the CUDA cores; the diagonal blocks are factored in FP64
+ *           arithmetic and rounded to FP32)
  *   info    device int, written asynchronously (see above); may not be NULL
  *   opt     NULL or options (prec must be NATIVE)
  *   work    may be NULL when jmg_workspace_size(JMG_OP_POTRF, ...) is 0
@@ -129,6 +131,7 @@ int jmg_potrf(int n, void* A, int lda, int dtype, int* info, const jmg_options* 
  * L Y = B, then back substitution L^T X = Y.
  *   L       device, lower(L) read; lda >= max(1, n)
  *   B       device, n x nrhs, overwritten with X; ldb >= max(1, n)
+ *   dtype   JMG_F64 or JMG_F32 (L and B of that type; the solve runs in it)
  * Asynchronous.
  */
 int jmg_potrs(int n, int nrhs, const void* L, int lda, void* B, int ldb, int dtype,
@@ -160,13 +163,15 @@ int jmg_potrs_static(int n, int nrhs, const void* L, int lda, void* B, int ldb, 
 
 /*
  * posv -- solve A X = B (paper: "Software design", potrs as one call).
- *   prec == NATIVE: potrf then potrs, in place (A becomes L), asynchronous.
+ *   prec == NATIVE: potrf then potrs, in place (A becomes L), asynchronous;
+ *     dtype JMG_F64 or JMG_F32.
  *   prec != NATIVE: A is PRESERVED (it is needed for the FP64 residual).  The
  *     factor is built in `work` with tensor-core trailing updates and used as
  *     the preconditioner of an FP64 refinement loop that stops when the
  *     backward error (see jmg_stats.bwd_err) is <= opt->tol.  This mode
  *     synchronises `stream` once per refinement iteration and returns only when
- *     X is final.  B is overwritten with X.
+ *     X is final.  B is overwritten with X.  FP64 data only (JMG_F32 returns
+ *     JMG_ERR_UNSUPPORTED).
  *   info    device int (potrf convention); may not be NULL
  *   stats   host pointer or NULL
  */
@@ -177,6 +182,7 @@ int jmg_posv(int n, int nrhs, void* A, int lda, void* B, int ldb, int dtype, int
 /*
  * logdet -- log det A = 2 sum_i log L_ii from a factor made by jmg_potrf
  * (paper: "Software design", potrs can also return log det A).
+ *   dtype   of L: JMG_F64 or JMG_F32 (the sum is formed in FP64 either way)
  *   out     device double, written asynchronously
  */
 int jmg_logdet(int n, const void* L, int lda, int dtype, double* out, void* stream);

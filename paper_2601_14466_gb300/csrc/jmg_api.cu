@@ -102,18 +102,21 @@ static T* at(void* work, size_t off) {
 }
 
 // ---------------------------------------------------------------- FP64 factor
-static int potrf_f64(int n, double* A, int lda, int nb, int* info, cudaStream_t s) {
+// Plain factorisation in the storage type T (double: FP64 throughout; float:
+// FP32 panel solves and trailing updates on the CUDA cores, the diagonal blocks
+// in FP64 arithmetic).
+template <typename T>
+static int potrf_plain(int n, T* A, int lda, int nb, int* info, cudaStream_t s) {
   for (int k = 0; k < n; k += nb) {
     const int kb = std::min(nb, n - k);
-    double* Akk = A + (size_t)k * lda + k;
+    T* Akk = A + (size_t)k * lda + k;
     JMG_TRY(launch_potf2(Akk, lda, kb, k, info, s));
     const int m = n - k - kb;
     if (m <= 0) break;
-    double* L21 = Akk + kb;
+    T* L21 = Akk + kb;
     JMG_TRY(launch_trsm(L21, lda, m, kb, Akk, info, s));
-    JMG_TRY(launch_gemm<double>(m, m, kb, L21, lda, MODE_N, L21, lda, MODE_T,
-                                A + (size_t)(k + kb) * lda + (k + kb), lda, OUT_SUB_LOWER, 1, info,
-                                s));
+    JMG_TRY(launch_gemm<T>(m, m, kb, L21, lda, MODE_N, L21, lda, MODE_T,
+                           A + (size_t)(k + kb) * lda + (k + kb), lda, OUT_SUB_LOWER, 1, info, s));
   }
   return JMG_OK;
 }
@@ -488,6 +491,21 @@ static int check_common(int n, int lda, int dtype) {
   return JMG_OK;
 }
 
+template <typename T>
+__global__ void k_logdet(int n, const T* __restrict__ L, int lda, double* __restrict__ out) {
+  // one CTA, fixed-order reduction (in FP64 for either storage type)
+  __shared__ double part[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += log((double)L[(size_t)i * lda + i]);
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = 2.0 * part[0];
+}
+
 }  // namespace jmg
 
 using namespace jmg;
@@ -543,10 +561,11 @@ int jmg_potrf(int n, void* A, int lda, int dtype, int* info, const jmg_options* 
   jmg_options o;
   opts_or_default(opt, &o);
   if (o.nb != 64 && o.nb != 128) return -6;
-  if (o.prec != JMG_PREC_NATIVE || dtype != JMG_F64) return JMG_ERR_UNSUPPORTED;
+  if (o.prec != JMG_PREC_NATIVE) return JMG_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   JMG_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
-  return potrf_f64(n, (double*)A, lda, o.nb, info, s);
+  if (dtype == JMG_F32) return potrf_plain<float>(n, (float*)A, lda, o.nb, info, s);
+  return potrf_plain<double>(n, (double*)A, lda, o.nb, info, s);
 }
 
 int jmg_potrs(int n, int nrhs, const void* L, int lda, void* B, int ldb, int dtype, void* work,
@@ -555,12 +574,15 @@ int jmg_potrs(int n, int nrhs, const void* L, int lda, void* B, int ldb, int dty
   if (nrhs < 0) return -2;
   if (lda < std::max(1, n)) return -4;
   if (ldb < std::max(1, n)) return -6;
-  if (dtype != JMG_F64) return dtype == JMG_F32 ? JMG_ERR_UNSUPPORTED : -7;
+  if (dtype != JMG_F64 && dtype != JMG_F32) return -7;
   if (n == 0 || nrhs == 0) return JMG_OK;
   if (!L) return -3;
   if (!B) return -5;
   if (!work || lwork < plain_solve_bytes(n, nrhs)) return JMG_ERR_WORKSPACE;
   if (reinterpret_cast<uintptr_t>(work) & 15) return JMG_ERR_ALIGN;
+  if (dtype == JMG_F32)
+    return solve_llt<float>(n, nrhs, (const float*)L, lda, (float*)B, ldb, (int*)work, nullptr,
+                            (cudaStream_t)stream);
   return solve_llt<double>(n, nrhs, (const double*)L, lda, (double*)B, ldb, (int*)work, nullptr,
                            (cudaStream_t)stream);
 }
@@ -571,7 +593,7 @@ int jmg_posv(int n, int nrhs, void* A, int lda, void* B, int ldb, int dtype, int
   if (nrhs < 0) return -2;
   if (lda < std::max(1, n)) return -4;
   if (ldb < std::max(1, n)) return -6;
-  if (dtype != JMG_F64) return dtype == JMG_F32 ? JMG_ERR_UNSUPPORTED : -7;
+  if (dtype != JMG_F64 && dtype != JMG_F32) return -7;
   if (!info) return -8;
   jmg_options o;
   opts_or_default(opt, &o);
@@ -588,12 +610,20 @@ int jmg_posv(int n, int nrhs, void* A, int lda, void* B, int ldb, int dtype, int
     if (nrhs > 0 && (!work || lwork < plain_solve_bytes(n, nrhs))) return JMG_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(work) & 15) return JMG_ERR_ALIGN;
     JMG_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
-    JMG_TRY(potrf_f64(n, (double*)A, lda, o.nb, info, s));
+    if (dtype == JMG_F32) {
+      JMG_TRY(potrf_plain<float>(n, (float*)A, lda, o.nb, info, s));
+      if (nrhs > 0)
+        JMG_TRY(solve_llt<float>(n, nrhs, (const float*)A, lda, (float*)B, ldb, (int*)work, info,
+                                 s));
+      return JMG_OK;
+    }
+    JMG_TRY(potrf_plain<double>(n, (double*)A, lda, o.nb, info, s));
     if (nrhs > 0)
       JMG_TRY(solve_llt<double>(n, nrhs, (const double*)A, lda, (double*)B, ldb, (int*)work, info,
                                 s));
     return JMG_OK;
   }
+  if (dtype == JMG_F32) return JMG_ERR_UNSUPPORTED;  // mixed modes refine FP64 data
   if (o.prec != JMG_PREC_BF16 && o.prec != JMG_PREC_FP16 && o.prec != JMG_PREC_FP8)
     return JMG_ERR_UNSUPPORTED;
   if (o.prec == JMG_PREC_FP8 && o.nb != 128) return -9;
@@ -604,27 +634,16 @@ int jmg_posv(int n, int nrhs, void* A, int lda, void* B, int ldb, int dtype, int
   return posv_mixed(n, nrhs, (const double*)A, lda, (double*)B, ldb, info, o, stats, work, s);
 }
 
-__global__ void k_logdet(int n, const double* __restrict__ L, int lda, double* __restrict__ out) {
-  // one CTA, fixed-order reduction
-  __shared__ double part[256];
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += log(L[(size_t)i * lda + i]);
-  part[threadIdx.x] = acc;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *out = 2.0 * part[0];
-}
-
 int jmg_logdet(int n, const void* L, int lda, int dtype, double* out, void* stream) {
   if (n < 0) return -1;
   if (lda < std::max(1, n)) return -3;
-  if (dtype != JMG_F64) return JMG_ERR_UNSUPPORTED;
+  if (dtype != JMG_F64 && dtype != JMG_F32) return -4;
   if (!out) return -5;
   if (n > 0 && !L) return -2;
-  k_logdet<<<1, 256, 0, (cudaStream_t)stream>>>(n, (const double*)L, lda, out);
+  if (dtype == JMG_F32)
+    k_logdet<float><<<1, 256, 0, (cudaStream_t)stream>>>(n, (const float*)L, lda, out);
+  else
+    k_logdet<double><<<1, 256, 0, (cudaStream_t)stream>>>(n, (const double*)L, lda, out);
   return launched();
 }
 

@@ -179,18 +179,25 @@ def workspace(op: int, n: int, nrhs: int, opts: Options | None, device) -> torch
 # ------------------------------------------------------------------ tensor helpers
 
 
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float64:
+        return JMG_F64
+    if t.dtype == torch.float32:
+        return JMG_F32
+    raise TypeError("float64 or float32 storage only, got %s" % t.dtype)
+
+
 def potrf_(A: torch.Tensor, *, nb: int = 128, info: torch.Tensor | None = None) -> torch.Tensor:
-    """Cholesky factorisation in place: lower(A) <- L (FP64, column-major).
+    """Cholesky factorisation in place: lower(A) <- L (FP64 or FP32, column-major).
     Returns the device info tensor (int32, 1 element); asynchronous."""
     _need_cuda(A)
-    if A.dtype != torch.float64:
-        raise TypeError("potrf_: FP64 only")
+    dt = _dtype_code(A)
     p, lda = _colmajor(A, "A")
     n = A.shape[0]
     if info is None:
         info = torch.zeros(1, dtype=torch.int32, device=A.device)
     o = default_options(nb=nb)
-    st = load().jmg_potrf(n, p, lda, JMG_F64, info.data_ptr(), ctypes.byref(o), None, 0,
+    st = load().jmg_potrf(n, p, lda, dt, info.data_ptr(), ctypes.byref(o), None, 0,
                           _stream(A.device))
     _chk(st, "jmg_potrf")
     return info
@@ -199,10 +206,13 @@ def potrf_(A: torch.Tensor, *, nb: int = 128, info: torch.Tensor | None = None) 
 def potrs_(L: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
     """Solve (L L^T) X = B in place on B (column-major); asynchronous."""
     _need_cuda(L, B)
+    dt = _dtype_code(L)
+    if B.dtype != L.dtype:
+        raise TypeError("potrs_: L and B must have the same dtype")
     pl, lda = _colmajor(L, "L")
     pb, ldb = _colmajor(B, "B")
     work = workspace(OP_POTRS, L.shape[0], B.shape[1], None, L.device)
-    st = load().jmg_potrs(L.shape[0], B.shape[1], pl, lda, pb, ldb, JMG_F64, work.data_ptr(),
+    st = load().jmg_potrs(L.shape[0], B.shape[1], pl, lda, pb, ldb, dt, work.data_ptr(),
                           work.numel(), _stream(L.device))
     _chk(st, "jmg_potrs")
     return B
@@ -241,8 +251,12 @@ def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1
     precision with tensor-core trailing updates and FP64 refinement; A is
     preserved.  Returns ``(X, SolveInfo)``; X is a new column-major tensor."""
     _need_cuda(A, B)
-    if A.dtype != torch.float64 or B.dtype != torch.float64:
-        raise TypeError("posv: FP64 storage only")
+    if A.dtype != B.dtype or A.dtype not in (torch.float64, torch.float32):
+        raise TypeError("posv: A and B must both be float64 (any mode) or both float32 "
+                        "(prec='fp64', i.e. the plain path in the storage type)")
+    dt = _dtype_code(A)
+    if dt == JMG_F32 and prec != "fp64":
+        raise TypeError("posv: the mixed modes refine FP64 data; float32 takes prec='fp64'")
     squeeze = B.dim() == 1
     if squeeze:
         B = B.reshape(-1, 1)
@@ -260,7 +274,7 @@ def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1
     if work is None:
         work = workspace(OP_POSV, n, nrhs, o, A.device)
     wp, wl = (work.data_ptr(), work.numel()) if work is not None else (None, 0)
-    st = load().jmg_posv(n, nrhs, pa, lda, px, ldx, JMG_F64, info.data_ptr(), ctypes.byref(o),
+    st = load().jmg_posv(n, nrhs, pa, lda, px, ldx, dt, info.data_ptr(), ctypes.byref(o),
                          ctypes.byref(stats), wp, wl, _stream(A.device))
     if o.prec == 0:
         info_h = int(info.item()) if check else 0
@@ -297,7 +311,8 @@ def logdet(L: torch.Tensor) -> torch.Tensor:
     _need_cuda(L)
     pl, lda = _colmajor(L, "L")
     out = torch.empty((), dtype=torch.float64, device=L.device)
-    _chk(load().jmg_logdet(L.shape[0], pl, lda, JMG_F64, out.data_ptr(), _stream(L.device)),
+    _chk(load().jmg_logdet(L.shape[0], pl, lda, _dtype_code(L), out.data_ptr(),
+                           _stream(L.device)),
          "jmg_logdet")
     return out
 
