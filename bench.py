@@ -53,7 +53,7 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 G
 
 # DRAM bytes (read + write) of one k_trsv_persist<float> launch, from one ncu
 # capture (profiles/k_trsv_persist_n16384_nrhs64.md); None where not captured.
-_SOLVE_TRAFFIC = {}
+_SOLVE_TRAFFIC = {(16384, 64): 542343680 + 5179136}
 
 
 def SOLVE_TRAFFIC_BYTES(n, nrhs):
@@ -478,7 +478,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--kappa", type=float, default=None)
-    ap.add_argument("--maxit", type=int, default=50)
+    ap.add_argument("--maxit", type=int, default=300)
     ap.add_argument("--refine", default="auto", choices=["ir", "pcg", "auto"])
     ap.add_argument("--resid", default="auto", choices=["auto", "fp64", "split"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -103,7 +103,7 @@ typedef struct {
 } jmg_stats;
 
 /* Fill *opt with the defaults: nb 128, NB 128, prec NATIVE, words 1, tol 1e-13,
- * maxit 50, refine AUTO, shift_retry 1, timing 0, reuse_factor 0, resid 0. */
+ * maxit 300, refine AUTO, shift_retry 1, timing 0, reuse_factor 0, resid 0. */
 void jmg_default_options(jmg_options* opt);
 
 /* Bytes of `work` that the call (op, n, nrhs, dtype, opt) needs; 0 is valid. */

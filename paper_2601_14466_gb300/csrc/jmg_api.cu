@@ -519,7 +519,7 @@ void jmg_default_options(jmg_options* o) {
   o->prec = JMG_PREC_NATIVE;
   o->words = 1;
   o->tol = 1e-13;
-  o->maxit = 50;
+  o->maxit = 300;
   o->refine = JMG_REFINE_AUTO;
   o->shift_retry = 1;
   o->timing = 0;

@@ -241,7 +241,7 @@ class SolveInfo:
 
 
 def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1, nb: int = 128,
-         tol: float = 1e-13, maxit: int = 50, refine: str = "auto", shift_retry: bool = True,
+         tol: float = 1e-13, maxit: int = 300, refine: str = "auto", shift_retry: bool = True,
          overwrite_a: bool = False, work: torch.Tensor | None = None, check: bool = True,
          timing: bool = False, reuse_factor: bool = False, resid: str = "auto"):
     """Solve A X = B for SPD A (lower triangle of the column-major A read).

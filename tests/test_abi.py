@@ -64,7 +64,7 @@ def test_illegal_arguments_are_rejected_on_the_host():
 
 def test_defaults_and_workspace():
     o = jmg.default_options()
-    assert (o.nb, o.prec, o.words, o.maxit, o.reuse_factor) == (128, 0, 1, 50, 0)
+    assert (o.nb, o.prec, o.words, o.maxit, o.reuse_factor) == (128, 0, 1, 300, 0)
     assert abs(o.tol - 1e-13) < 1e-30
     assert jmg.workspace_size(jmg.OP_POTRF, 1000, 1, o) == 0
     # the plain solves only need their tickets and flags
