@@ -22,10 +22,12 @@
 // per K split is stored.  R = B - sum of partials is formed by the same
 // reduction kernel as the CUDA-core residual.
 //
-// tcgen05 kernel, 320 threads: warp 0 issues TMA loads (8 X-slice tiles per
+// tcgen05 kernel, 576 threads: warp 0 issues TMA loads (8 X-slice tiles per
 // 64-wide K block, then 8 A-slice tiles through a 4-stage ring), warp 1 issues
-// the MMAs (M = 128, N = 16/32/64, K = 16; 144 per K block), warps 2-9 drain
-// TMEM (two per TMEM lane quarter).  All waits are bounded.
+// the MMAs (M = 128, K = 16, N = up to 256: consecutive X slices of one A
+// slice in one instruction), warps 2-17 drain
+// TMEM (up to four per TMEM lane quarter, 16 columns each).  All waits are
+// bounded.
 #include <algorithm>
 
 #include "kernels.h"
@@ -38,7 +40,7 @@ constexpr int BM = 128;     // rows per tile
 constexpr int BK = 64;      // K per block: 64 BF16 = one 128-byte swizzle row
 constexpr int WIN = 4;      // K blocks per exact accumulation window (256 values)
 constexpr int ASTAGES = 4;  // ring of A-slice tiles
-constexpr int THREADS = 320;  // warps 0-1 producer / MMA, 2-9 epilogue
+constexpr int THREADS = 576;  // warps 0-1 producer / MMA, 2-17 epilogue (16 columns each)
 constexpr int A_TILE = BM * BK * 2;  // 16 KiB
 
 // rint(x 2^(56-e)) for |x| < 2^e, formed from the bits of x with integer
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
       mbar_init(&aempty[i], 1);
     }
     mbar_init(accf, 1);
-    mbar_init(acce, N == 16 ? 4 : 8);
+    mbar_init(acce, N * 4 / 16);
     fence_mbar_init();
     prefetch_tmap(&tmA);
     prefetch_tmap(&tmX);
@@ -302,7 +304,7 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_f16(BM, N, 1);
+      constexpr int GMAX = (256 / N) < S ? (256 / N) : S;  // X slices per MMA
       long long g = 0;
       bool ok = true;
       for (int w = w0; w < w1 && ok; ++w) {
@@ -328,13 +330,19 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
             }
             tc_fence_after();
             const uint32_t ab = smem_u32(abuf + st * A_TILE);
-            for (int b = 0; b < S - a; ++b) {
-              const uint32_t dacc = tmem + (uint32_t)((a + b) * N);
+            // X slices b = 0 .. S-1-a feed levels d = a .. S-1.  The slices sit
+            // one after another in shared memory and the levels' accumulators
+            // one after another in TMEM, so GMAX consecutive slices make one
+            // MMA of N * GMAX columns (<= 256) that reads the A tile once.
+            for (int b0 = 0; b0 < S - a; b0 += GMAX) {
+              const int cnt = min(GMAX, S - a - b0);
+              const uint32_t idesc_g = idesc_f16(BM, N * cnt, 1);
+              const uint32_t dacc = tmem + (uint32_t)((a + b0) * N);
 #pragma unroll
               for (int kk = 0; kk < 4; ++kk) {
                 const bool first = (kb == kbw0) && (a == 0) && (kk == 0);
                 tc_mma_f16(dacc, sdesc_sw128(ab + kk * 32),
-                           sdesc_sw128(xb + b * X_TILE + kk * 32), idesc, first ? 0u : 1u);
+                           sdesc_sw128(xb + b0 * X_TILE + kk * 32), idesc_g, first ? 0u : 1u);
               }
             }
             tc_commit(&aempty[st]);
@@ -353,8 +361,8 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
     // ls = sum acc_d 2^(49-7d) (each window adds less than 2^45 to either, and
     // a CTA takes at most 256 windows, so both stay below 2^53).  Only the end
     // converts to FP64: sum_d acc_d 2^-7d = 2^-21 (hs + ls 2^-28), one rounding.
-    constexpr int EW = (N == 16) ? 4 : 8;  // epilogue warps with columns
-    constexpr int CW = N * 4 / EW;         // columns per epilogue warp (16 or 32)
+    constexpr int CW = 16;         // columns per epilogue warp
+    constexpr int EW = N * 4 / CW;  // epilogue warps with columns (4 per 64 columns)
     const int ew = warp - 2;
     const int q = warp & 3;
     const int ch = (ew >> 2) * CW;
