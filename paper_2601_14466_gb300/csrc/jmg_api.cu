@@ -123,30 +123,79 @@ static int potrf_plain(int n, T* A, int lda, int nb, int* info, cudaStream_t s) 
 
 // ---------------------------------------------------------------- mixed factor
 // Factor the FP32 working matrix W (lower) in place; info_f and err are device
-// ints of the workspace.
+// ints of the workspace.  Right-looking over 128-wide panels.  The update of
+// step k is split in two: the next panel's columns first, then the rest of the
+// trailing matrix on one SM fewer; the next diagonal block (one CTA, bound by
+// its serial chain) is factored on a second stream on the free SM while the
+// rest of the update runs.  The panel solve and the word split of step k+1
+// follow both on the caller's stream.
 static int factor_mixed(int n, float* W, int ldw, const jmg_options& o, const Plan& p,
                         void* work, int* info_f, int* err, cudaStream_t s) {
   const int nb = o.nb;
   void* PA = at<void>(work, p.off_PA);
   void* PB = split_pairs(o.words) > 1 ? at<void>(work, p.off_PB) : PA;
+  const bool fp8 = o.prec == JMG_PREC_FP8;
+  signed char* ex = fp8 ? at<signed char>(work, p.off_exp) : nullptr;
+  const int kext = fp8 ? nb : nb * split_pairs(o.words);
+  const size_t esz = fp8 ? 1 : 2;  // bytes per operand element
+  // the side stream and its events live for this call only
+  struct Side {
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t panel = nullptr, diag = nullptr;
+    ~Side() {
+      if (panel) cudaEventDestroy(panel);
+      if (diag) cudaEventDestroy(diag);
+      if (s2) cudaStreamDestroy(s2);
+    }
+  } side;
+  int prio_lo = 0, prio_hi = 0;
+  JMG_CUDA(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+  JMG_CUDA(cudaStreamCreateWithPriority(&side.s2, cudaStreamNonBlocking, prio_hi));
+  JMG_CUDA(cudaEventCreateWithFlags(&side.panel, cudaEventDisableTiming));
+  JMG_CUDA(cudaEventCreateWithFlags(&side.diag, cudaEventDisableTiming));
+  int dev = 0, nsm = 152;
+  JMG_CUDA(cudaGetDevice(&dev));
+  JMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+
+  JMG_TRY(launch_potf2(W, ldw, std::min(nb, n), 0, info_f, s));
   for (int k = 0; k < n; k += nb) {
     const int kb = std::min(nb, n - k);
     float* Wkk = W + (size_t)k * ldw + k;
-    JMG_TRY(launch_potf2(Wkk, ldw, kb, k, info_f, s));
     const int m = n - k - kb;
     if (m <= 0) break;
     float* L21 = Wkk + kb;
     JMG_TRY(launch_trsm(L21, ldw, m, kb, Wkk, info_f, s));
     float* W22 = W + (size_t)(k + kb) * ldw + (k + kb);
-    if (o.prec == JMG_PREC_FP8) {
-      signed char* ex = at<signed char>(work, p.off_exp);
+    if (fp8)
       JMG_TRY(launch_quant_fp8(m, kb, L21, ldw, PA, p.ldp, ex, s));
-      JMG_TRY(launch_syrk_fp8(m, m, kb, PA, p.ldp, ex, W22, ldw, err, s));
-    } else {
+    else
       JMG_TRY(launch_split_words(m, kb, L21, ldw, o.prec, o.words, PA, PB, p.ldp, s));
-      JMG_TRY(launch_syrk_tc(m, m, kb * split_pairs(o.words), PA, PB, p.ldp, o.prec, W22, ldw,
-                             err, s));
+    // (P) the next panel's columns (all m rows, the diagonal tile masked)
+    const int pc = std::min(nb, m);
+    if (fp8)
+      JMG_TRY(launch_syrk_fp8(m, pc, kext, PA, p.ldp, ex, W22, ldw, err, s));
+    else
+      JMG_TRY(launch_syrk_tc(m, pc, kext, PA, PB, p.ldp, o.prec, W22, ldw, err, s));
+    // the next diagonal block, beside the rest of the update
+    JMG_CUDA(cudaEventRecord(side.panel, s));
+    JMG_CUDA(cudaStreamWaitEvent(side.s2, side.panel, 0));
+    JMG_TRY(launch_potf2(W22, ldw, pc, k + kb, info_f, side.s2));
+    JMG_CUDA(cudaEventRecord(side.diag, side.s2));
+    // (R) the trailing matrix right of the next panel, leaving one SM free
+    const int mr = m - pc;
+    if (mr > 0) {
+      float* W33 = W22 + (size_t)pc * ldw + pc;
+      const size_t off = (size_t)pc * p.ldp * esz;  // operand rows pc ..
+      const void* PAr = static_cast<const char*>(PA) + off;
+      const void* PBr = static_cast<const char*>(PB) + off;
+      if (fp8)
+        JMG_TRY(launch_syrk_fp8(mr, mr, kext, PAr, p.ldp, ex + pc / 128, W33, ldw, err, s,
+                                nsm - 1));
+      else
+        JMG_TRY(launch_syrk_tc(mr, mr, kext, PAr, PBr, p.ldp, o.prec, W33, ldw, err, s,
+                               nsm - 1));
     }
+    JMG_CUDA(cudaStreamWaitEvent(s, side.diag, 0));
   }
   return JMG_OK;
 }

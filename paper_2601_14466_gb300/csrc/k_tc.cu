@@ -293,7 +293,7 @@ static int make_map(CUtensorMap* map, const void* base, int rows, int cols, int 
 template <int KIND>
 static int syrk_persistent(int m, int ncols, int kext, const CUtensorMap& ma, const CUtensorMap& mb,
                            int ab_fmt, const signed char* exps, float* C, int ldc, int* err,
-                           cudaStream_t s) {
+                           cudaStream_t s, int max_ctas) {
   static int attr_dev = -1, nsm = 0;
   int dev = 0;
   JMG_CUDA(cudaGetDevice(&dev));
@@ -305,14 +305,14 @@ static int syrk_persistent(int m, int ncols, int kext, const CUtensorMap& ma, co
   }
   const int TI = cdiv(m, tc::BM), TJ = cdiv(ncols, tc::BN);
   const long long ntiles = (long long)TJ * (TJ + 1) / 2 + (long long)(TI - TJ) * TJ;
-  const int grid = (int)std::min<long long>(ntiles, nsm);
+  const int grid = (int)std::min<long long>(ntiles, max_ctas > 0 ? std::min(max_ctas, nsm) : nsm);
   tc::k_syrk_tc<KIND><<<grid, tc::PTHREADS, tc::PSMEM_BYTES, s>>>(
       ma, mb, C, ldc, m, ncols, kext, ab_fmt, (int)ntiles, TJ, exps, err);
   return launched();
 }
 
 int launch_syrk_tc(int m, int ncols, int kext, const void* PA, const void* PB, int ldp, int prec,
-                   float* C, int ldc, int* err, cudaStream_t s) {
+                   float* C, int ldc, int* err, cudaStream_t s, int max_ctas) {
   if (m <= 0 || ncols <= 0 || kext <= 0) return JMG_OK;
   if (ncols > m) return JMG_ERR_UNSUPPORTED;
   if (kext % tc::BK || ldp % 64 || ldp < kext) return JMG_ERR_ALIGN;
@@ -324,11 +324,11 @@ int launch_syrk_tc(int m, int ncols, int kext, const void* PA, const void* PB, i
   JMG_TRY(make_map(&ma, PA, m, kext, ldp, 2, dt));
   JMG_TRY(make_map(&mb, PB, m, kext, ldp, 2, dt));
   return syrk_persistent<0>(m, ncols, kext, ma, mb, prec == JMG_PREC_BF16 ? 1 : 0, nullptr, C, ldc,
-                            err, s);
+                            err, s, max_ctas);
 }
 
 int launch_syrk_fp8(int m, int ncols, int kext, const void* Q, int ldq, const signed char* e,
-                    float* C, int ldc, int* err, cudaStream_t s) {
+                    float* C, int ldc, int* err, cudaStream_t s, int max_ctas) {
   if (m <= 0 || ncols <= 0 || kext <= 0) return JMG_OK;
   if (ncols > m) return JMG_ERR_UNSUPPORTED;
   if (kext % 128 || ldq % 128 || ldq < kext) return JMG_ERR_ALIGN;
@@ -336,7 +336,7 @@ int launch_syrk_fp8(int m, int ncols, int kext, const void* Q, int ldq, const si
   if (!e) return JMG_ERR_UNSUPPORTED;
   CUtensorMap mq;
   JMG_TRY(make_map(&mq, Q, m, kext, ldq, 1, CU_TENSOR_MAP_DATA_TYPE_UINT8));
-  return syrk_persistent<1>(m, ncols, kext, mq, mq, 0, e, C, ldc, err, s);
+  return syrk_persistent<1>(m, ncols, kext, mq, mq, 0, e, C, ldc, err, s, max_ctas);
 }
 
 }  // namespace jmg

@@ -143,11 +143,12 @@ int launch_sym_grad(int n, int nrhs, const double* Bb, int ldb, const double* X,
 // ---- tensor-core trailing update (k_tc.cu)
 // C (m x ncols, lower trapezoid: rows >= columns) -= PA PB^T, PA/PB: m x kext
 // row-major 16-bit words; ncols <= m.
+// max_ctas > 0 caps the persistent grid (to leave SMs free for concurrent work).
 int launch_syrk_tc(int m, int ncols, int kext, const void* PA, const void* PB, int ldp, int prec,
-                   float* C, int ldc, int* err, cudaStream_t s);
+                   float* C, int ldc, int* err, cudaStream_t s, int max_ctas = 0);
 // FP8 e4m3 variant: Q (m x kext bytes, row-major, ldq), C -= 2^-(e[ti]+e[tj]) Q_ti Q_tj^T
 int launch_syrk_fp8(int m, int ncols, int kext, const void* Q, int ldq, const signed char* e,
-                    float* C, int ldc, int* err, cudaStream_t s);
+                    float* C, int ldc, int* err, cudaStream_t s, int max_ctas = 0);
 // Quantise the FP32 panel L21 (m x kb, ldw) to e4m3 with one power-of-two scale
 // per 128-row tile: e = floor(log2(448 / amax)) clamped to [-126, 126] (0 for an
 // all-zero tile), Q = rn_satfinite(x * 2^e), row-major m x kb (ldq bytes).
