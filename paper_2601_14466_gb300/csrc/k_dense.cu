@@ -624,125 +624,6 @@ template int launch_gemm<float>(int, int, int, const float*, int, int, const flo
                                 float*, int, int, int, const int*, cudaStream_t);
 
 // ============================================================================
-// Diagonal-block triangular solve, one warp per right-hand side.  Lane l holds
-// rows l, l+32, l+64, l+96 of its column.  Forward (L y = b): for each j the
-// owner lane divides by L_jj, broadcasts y_j, every lane updates its rows below
-// j.  Backward (L^T x = y): j descends, the update runs over rows above j with
-// row j of L (L^T's column j).
-// ============================================================================
-template <typename T, int NBMAX>
-__global__ void __launch_bounds__(256) k_trsv_diag(int kb, int nrhs, const T* __restrict__ L,
-                                                   int lda, T* __restrict__ B, int ldb, int trans,
-                                                   const int* __restrict__ info) {
-  if (info && *(volatile const int*)info != 0) return;
-  extern __shared__ __align__(16) unsigned char sm_trsv[];
-  T* Ls = reinterpret_cast<T*>(sm_trsv);
-  const int ld = kb + 1;
-  for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
-    int i = idx % kb, j = idx / kb;
-    Ls[j * ld + i] = (i >= j) ? L[(size_t)j * lda + i] : T(0);
-  }
-  __syncthreads();
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int col = blockIdx.x * 8 + warp;
-  if (col >= nrhs) return;
-  constexpr int Q = NBMAX / 32;
-  T b[Q];
-  T* bc = B + (size_t)col * ldb;
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    int r = lane + 32 * q;
-    b[q] = (r < kb) ? bc[r] : T(0);
-  }
-  if (trans == 0) {
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      for (int jj = 0; jj < 32; ++jj) {
-        const int j = q * 32 + jj;
-        if (j >= kb) break;
-        if (lane == jj) b[q] = b[q] / Ls[j * ld + j];
-        const T y = __shfl_sync(0xffffffffu, b[q], jj);
-#pragma unroll
-        for (int p = q; p < Q; ++p) {
-          int r = lane + 32 * p;
-          if (r > j && r < kb) b[p] -= Ls[j * ld + r] * y;
-        }
-      }
-    }
-  } else {
-#pragma unroll
-    for (int q = Q - 1; q >= 0; --q) {
-      for (int jj = 31; jj >= 0; --jj) {
-        const int j = q * 32 + jj;
-        if (j >= kb) continue;
-        if (lane == jj) b[q] = b[q] / Ls[j * ld + j];
-        const T x = __shfl_sync(0xffffffffu, b[q], jj);
-#pragma unroll
-        for (int p = 0; p <= q; ++p) {
-          int r = lane + 32 * p;
-          if (r < j) b[p] -= Ls[r * ld + j] * x;
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    int r = lane + 32 * q;
-    if (r < kb) bc[r] = b[q];
-  }
-}
-
-template <typename T>
-int launch_trsv_diag(int kb, int nrhs, const T* L, int lda, T* B, int ldb, int trans,
-                     const int* info, cudaStream_t s) {
-  if (kb <= 0 || nrhs <= 0) return JMG_OK;
-  size_t smem = (size_t)kb * (kb + 1) * sizeof(T);
-  dim3 grid(cdiv(nrhs, 8));
-  if (kb <= 64) {
-    auto k = k_trsv_diag<T, 64>;
-    JMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k<<<grid, 256, smem, s>>>(kb, nrhs, L, lda, B, ldb, trans, info);
-  } else {
-    auto k = k_trsv_diag<T, 128>;
-    JMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k<<<grid, 256, smem, s>>>(kb, nrhs, L, lda, B, ldb, trans, info);
-  }
-  return launched();
-}
-template int launch_trsv_diag<double>(int, int, const double*, int, double*, int, int, const int*,
-                                      cudaStream_t);
-template int launch_trsv_diag<float>(int, int, const float*, int, float*, int, int, const int*,
-                                     cudaStream_t);
-
-// Blocked right-looking solves: forward over diagonal blocks with a GEMM update
-// of the rows below, then backward with a GEMM update of the rows above.
-template <typename T>
-int blocked_potrs(int n, int nrhs, const T* L, int lda, T* B, int ldb, int nb, const int* info,
-                  cudaStream_t s) {
-  for (int k = 0; k < n; k += nb) {
-    int kb = min(nb, n - k);
-    JMG_TRY(launch_trsv_diag<T>(kb, nrhs, L + (size_t)k * lda + k, lda, B + k, ldb, 0, info, s));
-    int m = n - k - kb;
-    if (m > 0)
-      JMG_TRY(launch_gemm<T>(m, nrhs, kb, L + (size_t)k * lda + k + kb, lda, MODE_N, B + k, ldb,
-                             MODE_N, B + k + kb, ldb, OUT_SUB, 1, info, s));
-  }
-  int last = ((n - 1) / nb) * nb;
-  for (int k = last; k >= 0; k -= nb) {
-    int kb = min(nb, n - k);
-    JMG_TRY(launch_trsv_diag<T>(kb, nrhs, L + (size_t)k * lda + k, lda, B + k, ldb, 1, info, s));
-    if (k > 0)  // B[0:k] -= L[k:k+kb, 0:k]^T X_k
-      JMG_TRY(launch_gemm<T>(k, nrhs, kb, L + k, lda, MODE_T, B + k, ldb, MODE_N, B, ldb,
-                             OUT_SUB, 1, info, s));
-  }
-  return JMG_OK;
-}
-template int blocked_potrs<double>(int, int, const double*, int, double*, int, int, const int*,
-                                   cudaStream_t);
-template int blocked_potrs<float>(int, int, const float*, int, float*, int, int, const int*,
-                                  cudaStream_t);
-
-// ============================================================================
 // FP64 residual R = B - A X (A symmetric, lower stored): split-K partial sums of
 // A X through the tiled GEMM (mode S), then a fixed-order reduction that also
 // records the per-column infinity norms of r, x and b.

@@ -37,12 +37,6 @@ template <typename T>
 int launch_gemm(int m, int n, int k, const T* A, int lda, int amode, const T* B, int ldb,
                 int bmode, T* C, int ldc, int out, int splits, const int* info, cudaStream_t s);
 
-// Triangular solve with the diagonal block L (kb x kb) for nrhs columns of B
-// (kb x nrhs, ldb): trans == 0: L Y = B;  trans == 1: L^T X = B.
-template <typename T>
-int launch_trsv_diag(int kb, int nrhs, const T* L, int lda, T* B, int ldb, int trans,
-                     const int* info, cudaStream_t s);
-
 // One-launch blocked solve with the whole factor, in place on B:
 // trans == 0: L Y = B;  trans == 1: L^T X = B.  `sync` holds
 // trsv_sync_ints(n, nrhs) ints of scratch (tickets, finished-block counters, per-block flags, error word).
@@ -57,11 +51,6 @@ int solve_llt(int n, int nrhs, const T* L, int lda, T* B, int ldb, int* sync, in
   JMG_TRY(launch_trsv_persist<T>(n, nrhs, L, lda, B, ldb, 0, sync, info, s));
   return launch_trsv_persist<T>(n, nrhs, L, lda, B, ldb, 1, sync, info, s);
 }
-
-// Blocked solves with the whole factor: L L^T X = B, in place on B.
-template <typename T>
-int blocked_potrs(int n, int nrhs, const T* L, int lda, T* B, int ldb, int nb, const int* info,
-                  cudaStream_t s);
 
 // ---- mixed-precision helpers
 // W (FP32, ldw) <- lower(A) (FP64), lower triangle only; plus shift on the diagonal.
