@@ -405,23 +405,53 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
   } guard{c.ev};
 
   const double t0 = now_ms();
+  // The prologue of the refinement -- ||A||_inf, and the row maxima and slices
+  // of A for the split residual -- only feeds the first residual: it runs on a
+  // low-priority side stream beside the factorisation and the initial solve.
+  // Every return path leaves `s` waiting for it (stream order keeps the
+  // workspace alive for it).
+  struct Prologue {
+    cudaStream_t main = nullptr, s3 = nullptr;
+    cudaEvent_t start = nullptr, done = nullptr;
+    bool pending = false;
+    int wait() {
+      if (pending) JMG_CUDA(cudaStreamWaitEvent(main, done, 0));
+      pending = false;
+      return JMG_OK;
+    }
+    ~Prologue() {
+      (void)wait();
+      if (start) cudaEventDestroy(start);
+      if (done) cudaEventDestroy(done);
+      if (s3) cudaStreamDestroy(s3);
+    }
+  } pro;
+  pro.main = s;
   if (!o.reuse_factor) {
+    int prio_lo = 0, prio_hi = 0;
+    JMG_CUDA(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+    JMG_CUDA(cudaStreamCreateWithPriority(&pro.s3, cudaStreamNonBlocking, prio_lo));
+    JMG_CUDA(cudaEventCreateWithFlags(&pro.start, cudaEventDisableTiming));
+    JMG_CUDA(cudaEventCreateWithFlags(&pro.done, cudaEventDisableTiming));
+    JMG_CUDA(cudaEventRecord(pro.start, s));  // A and the workspace are ready here
+    JMG_CUDA(cudaStreamWaitEvent(pro.s3, pro.start, 0));
     if (p.split) {  // one pass for the row sums (||A||_inf) and row maxima (slice scales)
       double* rowmax = at<double>(work, p.off_ozrow);
-      JMG_TRY(launch_row_stats(n, A, lda, c.rowsum, rowmax, s));
-      JMG_TRY(launch_max_reduce(n, c.rowsum, &c.dsc[0], s));
-      JMG_TRY(oz_slice_a(n, A, lda, rowmax, at<char>(work, p.off_ozA), s));
+      JMG_TRY(launch_row_stats(n, A, lda, c.rowsum, rowmax, pro.s3));
+      JMG_TRY(launch_max_reduce(n, c.rowsum, &c.dsc[0], pro.s3));
+      JMG_TRY(oz_slice_a(n, A, lda, rowmax, at<char>(work, p.off_ozA), pro.s3));
     } else {
-      JMG_TRY(launch_norm_inf(n, A, lda, c.rowsum, &c.dsc[0], s));
+      JMG_TRY(launch_norm_inf(n, A, lda, c.rowsum, &c.dsc[0], pro.s3));
     }
+    JMG_CUDA(cudaEventRecord(pro.done, pro.s3));
+    pro.pending = true;
     JMG_TRY(launch_diag_max(n, A, lda, &c.dsc[2], s));
     JMG_CUDA(cudaMemsetAsync(&c.dsc[1], 0, sizeof(double), s));
   }
-  double h3[3] = {0, 0, 0};
-  JMG_TRY(sync_read(h3, c.dsc, sizeof(h3), s));
-  S.anorm = h3[0];
-  double shift = h3[1];
-  const double dmax = h3[2];
+  double h2[2] = {0, 0};  // shift, max_i a_ii
+  JMG_TRY(sync_read(h2, &c.dsc[1], sizeof(h2), s));
+  double shift = h2[0];
+  const double dmax = h2[1];
   // unit roundoff of the factor: the split words, but never below FP32's
   const double u_f =
       o.prec == JMG_PREC_FP8
@@ -480,6 +510,7 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
     const double t2 = now_ms();
     S.t_solve_ms += t2 - t1;
 
+    JMG_TRY(pro.wait());  // the residual needs ||A||_inf and the slices of A
     // refinement: classic IR, switching to PCG when IR is slow or diverges
     bool use_pcg = (o.refine == JMG_REFINE_PCG);
     double prev = INFINITY;
@@ -528,7 +559,7 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
   }
   JMG_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
   JMG_TRY(launch_copy2d(n, nrhs, c.X, n, B, ldb, s));
-  JMG_CUDA(cudaStreamSynchronize(s));
+  JMG_TRY(sync_read(&S.anorm, &c.dsc[0], sizeof(double), s));
   S.status = converged ? JMG_OK : JMG_ERR_NOT_CONVERGED;
   return S.status;
 }

@@ -29,7 +29,7 @@ def _check(A, B, X, kappa, tol=1e-13):
 
 @pytest.mark.parametrize("prec,words", [("bf16", 1), ("bf16", 2), ("bf16", 3), ("fp16", 1),
                                         ("fp16", 2)])
-@pytest.mark.parametrize("n,nrhs", [(130, 1), (700, 4), (1100, 16)])
+@pytest.mark.parametrize("n,nrhs", [(64, 3), (130, 1), (257, 2), (700, 4), (1100, 16)])
 def test_posv_mixed_gram(prec, words, n, nrhs):
     A = inputs.gram_shift(n, 1.0, seed=inputs.seed_for("mixed", n))
     Xt = inputs.uniform(n, nrhs, seed=5)
@@ -43,6 +43,21 @@ def test_posv_mixed_gram(prec, words, n, nrhs):
     _check(A, B, X, kappa=10.0)
     # A is preserved bit for bit (NaN canary in the upper triangle included)
     assert torch.equal(torch.nan_to_num(Ad, nan=7.0), torch.nan_to_num(A_before, nan=7.0))
+
+
+@pytest.mark.parametrize("n", [100, 640, 1001])
+def test_posv_mixed_nb64(n):
+    # 64-wide panels: the diagonal factor, the panel solve and the split update
+    # at half width (and the overlap of the next diagonal block with the rest)
+    A = inputs.gram_shift(n, 1.0, seed=inputs.seed_for("nb64", n))
+    Xt = inputs.uniform(n, 5, seed=6)
+    B = inputs.rhs_from(A, Xt)
+    Ad, _ = to_dev_colmajor(lower_only(A))
+    Bd, _ = to_dev_colmajor(B)
+    X, si = jmg.posv(Ad, Bd, prec="bf16", words=2, nb=64)
+    assert si.status == 0 and si.info == 0
+    assert si.bwd_err <= 1e-13
+    _check(A, B, X, kappa=10.0)
 
 
 @pytest.mark.parametrize("kappa,prec,words", [(1e2, "bf16", 1), (1e4, "bf16", 2),
