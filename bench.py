@@ -64,6 +64,23 @@ def nominal_flops(n, nrhs):
     return n ** 3 / 3.0 + 2.0 * n * n * nrhs
 
 
+def max_over_ranks(values, world, device="cpu"):
+    """Elementwise max of a list of floats over all ranks (replicas run the same
+    steps; the slowest rank sets the job time)."""
+    import torch
+
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def replica_value(world, flops_per_step, steps, t_max_s):
+    """Whole-job TFLOP/s of `world` independent replicas, each doing `steps`
+    steps of `flops_per_step`, in the max-over-ranks time t_max_s."""
+    return world * flops_per_step * steps / t_max_s / 1e12
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -298,14 +315,11 @@ def run_ours(args, w, rank, world):
         del A_d, A_h
 
     # ---- across ranks: max time
-    times = torch.tensor([t_mixed, t_f64 or 0.0, t_e2e or 0.0], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
-    t_mixed, tf, te = [float(v) for v in times.cpu()]
+    t_mixed, tf, te = max_over_ranks([t_mixed, t_f64 or 0.0, t_e2e or 0.0], world, dev)
     t_f64 = tf if f64_steps > 0 else None
     t_e2e = te if e2e_steps > 0 else None
 
-    value = world * F * args.steps / t_mixed / 1e12
+    value = replica_value(world, F, args.steps, t_mixed)
     # Rooflines, from the library's CUDA events inside the timed steps (timing=True
     # records events around the solves, the residual products and the factor only).
     peaks = load_peaks()
@@ -387,14 +401,14 @@ def run_ours(args, w, rank, world):
         "clocks": clocks,
     }
     if t_f64 is not None:
-        fp64_value = world * F * f64_steps / t_f64 / 1e12
+        fp64_value = replica_value(world, F, f64_steps, t_f64)
         out["fp64"] = {"value": round(fp64_value, 4), "unit": "TFLOP/s",
                        "ms_per_step": round(t_f64 * 1e3 / f64_steps, 3), "steps": f64_steps,
                        "bwd_err": eta64,
                        "frac_of_fp64_nominal": round(fp64_value / world / FP64_NOMINAL_TFLOPS, 4)}
         out["speedup_mixed_vs_fp64"] = round((t_f64 / f64_steps) / (t_mixed / args.steps), 3)
     if t_e2e is not None:
-        out["e2e"] = {"value": round(world * F * e2e_steps / t_e2e / 1e12, 4), "unit": "TFLOP/s",
+        out["e2e"] = {"value": round(replica_value(world, F, e2e_steps, t_e2e), 4), "unit": "TFLOP/s",
                       "ms_per_step": round(t_e2e * 1e3 / e2e_steps, 3),
                       "h2d_bytes_per_step": n * n * 8 + n * nrhs * 8,
                       "d2h_bytes_per_step": n * nrhs * 8}
