@@ -180,6 +180,26 @@ int jmg_posv(int n, int nrhs, void* A, int lda, void* B, int ldb, int dtype, int
              void* stream);
 
 /*
+ * posv_batched -- many small independent systems A_b X_b = B_b (b = 0 .. batch-1)
+ * in one call: every A_b = L_b L_b^T in place, then X_b over B_b.  The paper's
+ * potrs is a batched primitive of its framework ("Summary": it composes with
+ * the framework's transformations, including vectorisation over a batch);
+ * this is its small-matrix form, one CTA per system.
+ *   n       order of every A_b, 0 <= n <= 128 (larger: JMG_ERR_UNSUPPORTED)
+ *   A       device; A_b = A + b * strideA, column-major, lower read, becomes L_b;
+ *           lda >= max(1, n), strideA >= lda * n (elements)
+ *   B       device; B_b = B + b * strideB, n x nrhs, overwritten with X_b;
+ *           ldb >= max(1, n), strideB >= ldb * nrhs (elements)
+ *   dtype   JMG_F64 or JMG_F32 (the plain path in the storage type)
+ *   info    device int[batch], written asynchronously: info[b] = 0, or k > 0 when
+ *           the leading minor of order k of A_b is not positive definite (that
+ *           B_b is then left unchanged)
+ * Asynchronous; allocates nothing.
+ */
+int jmg_posv_batched(int n, int nrhs, int batch, void* A, int lda, long long strideA, void* B,
+                     int ldb, long long strideB, int dtype, int* info, void* stream);
+
+/*
  * logdet -- log det A = 2 sum_i log L_ii from a factor made by jmg_potrf
  * (paper: "Software design", potrs can also return log det A).
  *   dtype   of L: JMG_F64 or JMG_F32 (the sum is formed in FP64 either way)

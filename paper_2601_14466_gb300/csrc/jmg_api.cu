@@ -714,6 +714,28 @@ int jmg_posv(int n, int nrhs, void* A, int lda, void* B, int ldb, int dtype, int
   return posv_mixed(n, nrhs, (const double*)A, lda, (double*)B, ldb, info, o, stats, work, s);
 }
 
+int jmg_posv_batched(int n, int nrhs, int batch, void* A, int lda, long long strideA, void* B,
+                     int ldb, long long strideB, int dtype, int* info, void* stream) {
+  if (n < 0) return -1;
+  if (nrhs < 0) return -2;
+  if (batch < 0) return -3;
+  if (lda < std::max(1, n)) return -5;
+  if (strideA < (long long)lda * n) return -6;
+  if (ldb < std::max(1, n)) return -8;
+  if (strideB < (long long)ldb * nrhs) return -9;
+  if (dtype != JMG_F64 && dtype != JMG_F32) return -10;
+  if (!info) return -11;
+  if (n > 128) return JMG_ERR_UNSUPPORTED;
+  if (batch > 0 && n > 0 && !A) return -4;
+  if (batch > 0 && n > 0 && nrhs > 0 && !B) return -7;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == JMG_F32)
+    return posv_small_batched<float>(n, nrhs, batch, (float*)A, lda, strideA, (float*)B, ldb,
+                                     strideB, info, s);
+  return posv_small_batched<double>(n, nrhs, batch, (double*)A, lda, strideA, (double*)B, ldb,
+                                    strideB, info, s);
+}
+
 int jmg_logdet(int n, const void* L, int lda, int dtype, double* out, void* stream) {
   if (n < 0) return -1;
   if (lda < std::max(1, n)) return -3;

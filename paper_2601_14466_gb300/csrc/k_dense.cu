@@ -83,8 +83,8 @@ JMG_DEV void load4<double>(const double* p, double (&v)[4]) {
 }  // namespace pdiag
 
 template <typename T>
-__global__ void __launch_bounds__(pdiag::TH) k_potrf_diag(T* __restrict__ A, int lda, int kb,
-                                                          int koff, int* __restrict__ info) {
+JMG_DEV void potrf_diag_body(T* __restrict__ A, int lda, int kb, int koff,
+                             int* __restrict__ info) {
   using namespace pdiag;
   extern __shared__ __align__(16) unsigned char sm_diag[];
   T* sa = reinterpret_cast<T*>(sm_diag);  // kb columns, LD apart: sa[c * LD + r] = a_rc
@@ -248,6 +248,100 @@ __global__ void __launch_bounds__(pdiag::TH) k_potrf_diag(T* __restrict__ A, int
   }
   if (t == 0 && fail) atomicCAS(info, 0, koff + fail);
 }
+
+template <typename T>
+__global__ void __launch_bounds__(pdiag::TH) k_potrf_diag(T* __restrict__ A, int lda, int kb,
+                                                          int koff, int* __restrict__ info) {
+  potrf_diag_body<T>(A, lda, kb, koff, info);
+}
+
+// Batched: CTA b factors the n x n system A + b * sA (n <= 128) with info[b].
+template <typename T>
+__global__ void __launch_bounds__(pdiag::TH) k_potrf_diag_batched(T* __restrict__ A, int lda,
+                                                                  long long sA, int n,
+                                                                  int* __restrict__ info) {
+  potrf_diag_body<T>(A + (size_t)blockIdx.x * sA, lda, n, 0, info + blockIdx.x);
+}
+
+// Batched solve with the factors of k_potrf_diag_batched: CTA b solves
+// (L_b L_b^T) X_b = B_b in place on B + b * sB, 64 right-hand sides per pass,
+// one thread per right-hand side: forward then back substitution against L_b in
+// shared memory (FP64 or FP32 as stored).  Systems with info[b] != 0 are left
+// alone.
+namespace pbat {
+constexpr int TH = 64;
+}
+template <typename T>
+__global__ void __launch_bounds__(pbat::TH) k_potrs_small(int n, int nrhs, const T* __restrict__ L,
+                                                          int lda, long long sA, T* __restrict__ B,
+                                                          int ldb, long long sB,
+                                                          const int* __restrict__ info) {
+  using pbat::TH;
+  const int b = blockIdx.x;
+  if (info[b] != 0) return;
+  extern __shared__ __align__(16) unsigned char sm_small[];
+  T* Ls = reinterpret_cast<T*>(sm_small);  // Ls[c * (n + 1) + r] = L(r, c)
+  T* Xs = Ls + (size_t)n * (n + 1);        // Xs[r * (TH + 1) + t] = x_r of column t
+  const int ldl = n + 1, ldx = TH + 1;
+  const T* Lb = L + (size_t)b * sA;
+  T* Bb = B + (size_t)b * sB;
+  const int t = threadIdx.x;
+  for (int idx = t; idx < n * n; idx += TH) {
+    const int r = idx % n, c = idx / n;
+    if (r >= c) Ls[c * ldl + r] = Lb[(size_t)c * lda + r];
+  }
+  for (int c0 = 0; c0 < nrhs; c0 += TH) {
+    const int nc = min(TH, nrhs - c0);
+    __syncthreads();  // L is in place; the previous pass is done with Xs
+    for (int idx = t; idx < n * nc; idx += TH) {  // coalesced down the columns
+      const int r = idx % n, c = idx / n;
+      Xs[r * ldx + c] = Bb[(size_t)(c0 + c) * ldb + r];
+    }
+    __syncthreads();
+    if (t < nc) {
+      for (int i = 0; i < n; ++i) {  // L y = b
+        const T y = Xs[i * ldx + t] / Ls[i * ldl + i];
+        Xs[i * ldx + t] = y;
+        for (int k = i + 1; k < n; ++k) Xs[k * ldx + t] -= Ls[i * ldl + k] * y;
+      }
+      for (int i = n - 1; i >= 0; --i) {  // L^T x = y
+        const T x = Xs[i * ldx + t] / Ls[i * ldl + i];
+        Xs[i * ldx + t] = x;
+        for (int k = 0; k < i; ++k) Xs[k * ldx + t] -= Ls[k * ldl + i] * x;
+      }
+    }
+    __syncthreads();
+    for (int idx = t; idx < n * nc; idx += TH) {
+      const int r = idx % n, c = idx / n;
+      Bb[(size_t)(c0 + c) * ldb + r] = Xs[r * ldx + c];
+    }
+  }
+}
+
+template <typename T>
+int posv_small_batched(int n, int nrhs, int batch, T* A, int lda, long long sA, T* B, int ldb,
+                       long long sB, int* info, cudaStream_t s) {
+  if (n > pdiag::KB) return JMG_ERR_UNSUPPORTED;
+  JMG_CUDA(cudaMemsetAsync(info, 0, sizeof(int) * (size_t)batch, s));
+  if (n == 0 || batch == 0) return JMG_OK;
+  {
+    auto k = k_potrf_diag_batched<T>;
+    JMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(pdiag::KB * pdiag::LD * sizeof(T))));
+    k<<<batch, pdiag::TH, (size_t)n * pdiag::LD * sizeof(T), s>>>(A, lda, sA, n, info);
+    JMG_TRY(launched());
+  }
+  if (nrhs == 0) return JMG_OK;
+  auto k = k_potrs_small<T>;
+  const size_t smem = sizeof(T) * ((size_t)n * (n + 1) + (size_t)n * (pbat::TH + 1));
+  JMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k<<<batch, pbat::TH, smem, s>>>(n, nrhs, A, lda, sA, B, ldb, sB, info);
+  return launched();
+}
+template int posv_small_batched<double>(int, int, int, double*, int, long long, double*, int,
+                                        long long, int*, cudaStream_t);
+template int posv_small_batched<float>(int, int, int, float*, int, long long, float*, int,
+                                       long long, int*, cudaStream_t);
 
 template <typename T>
 static int potf2_impl(T* A, int lda, int kb, int koff, int* info, cudaStream_t s) {

@@ -37,6 +37,12 @@ template <typename T>
 int launch_gemm(int m, int n, int k, const T* A, int lda, int amode, const T* B, int ldb,
                 int bmode, T* C, int ldc, int out, int splits, const int* info, cudaStream_t s);
 
+// Batched small systems (n <= 128): factor every A_b = L_b L_b^T in place
+// (info[b], 0-based batch index) and solve (L_b L_b^T) X_b = B_b in place.
+template <typename T>
+int posv_small_batched(int n, int nrhs, int batch, T* A, int lda, long long sA, T* B, int ldb,
+                       long long sB, int* info, cudaStream_t s);
+
 // One-launch blocked solve with the whole factor, in place on B:
 // trans == 0: L Y = B;  trans == 1: L^T X = B.  `sync` holds
 // trsv_sync_ints(n, nrhs) ints of scratch (tickets, finished-block counters, per-block flags, error word).

@@ -89,6 +89,8 @@ _SIGS = {
     "jmg_dev_norm_inf": (_I, [_I, _P, _I, _P, _P, _SZ, _P]),
     "jmg_dev_probe": (_I, [_I, _I, _I, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "jmg_dev_launch_count": (ctypes.c_longlong, []),
+    "jmg_posv_batched": (_I, [_I, _I, _I, _P, _I, ctypes.c_longlong, _P, _I, ctypes.c_longlong, _I,
+                              _P, _P]),
 }
 
 
@@ -291,6 +293,30 @@ def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1
         if check and st != 0:
             raise JmgError(st, "jmg_posv")
     return (X[:, 0] if squeeze else X), si
+
+
+def posv_batched(A: torch.Tensor, B: torch.Tensor):
+    """Solve many small SPD systems at once: A (batch, n, n), symmetric (its
+    row- and column-major forms coincide; the lower triangle is read), B
+    (batch, n, nrhs); FP64 or FP32, n <= 128.  Returns ``(X, L, info)``: X
+    (batch, n, nrhs) new, L the factors (a new (batch, n, n) tensor whose
+    transpose per system holds L in its lower triangle), info (batch,) int32;
+    asynchronous."""
+    _need_cuda(A, B)
+    if A.dim() != 3 or B.dim() != 3 or A.shape[0] != B.shape[0] or A.shape[1] != A.shape[2] \
+            or B.shape[1] != A.shape[1]:
+        raise ValueError("posv_batched: A (batch, n, n) and B (batch, n, nrhs)")
+    if A.dtype != B.dtype:
+        raise TypeError("posv_batched: A and B must have the same dtype")
+    dt = _dtype_code(A)
+    batch, n, nrhs = A.shape[0], A.shape[1], B.shape[2]
+    Lw = A.transpose(1, 2).contiguous()        # per system: column-major copy of A
+    Xw = B.transpose(1, 2).contiguous()        # (batch, nrhs, n): column-major per system
+    info = torch.zeros(max(batch, 1), dtype=torch.int32, device=A.device)
+    st = load().jmg_posv_batched(n, nrhs, batch, Lw.data_ptr(), max(n, 1), n * n, Xw.data_ptr(),
+                                 max(n, 1), n * nrhs, dt, info.data_ptr(), _stream(A.device))
+    _chk(st, "jmg_posv_batched")
+    return Xw.transpose(1, 2), Lw, info[:batch]
 
 
 def sym_grad(Bbar: torch.Tensor, X: torch.Tensor) -> torch.Tensor:

@@ -107,3 +107,19 @@ def test_struct_layouts_match_the_header(tmp_path):
     want = [ctypes.sizeof(jmg.Options), ctypes.sizeof(jmg.Stats), jmg.Stats.eta_hist.offset,
             jmg.Stats.n_solve.offset, jmg.Stats.t_factor_gpu_ms.offset]
     assert got == want
+
+
+def test_posv_batched_argument_checks():
+    lib = jmg.load()
+    f = lib.jmg_posv_batched
+    # (n, nrhs, batch, A, lda, sA, B, ldb, sB, dtype, info, stream)
+    assert f(-1, 1, 1, 256, 1, 1, 256, 1, 1, jmg.JMG_F64, 256, None) == -1
+    assert f(4, -1, 1, 256, 4, 16, 256, 4, 4, jmg.JMG_F64, 256, None) == -2
+    assert f(4, 1, -1, 256, 4, 16, 256, 4, 4, jmg.JMG_F64, 256, None) == -3
+    assert f(4, 1, 1, 256, 3, 16, 256, 4, 4, jmg.JMG_F64, 256, None) == -5
+    assert f(4, 1, 1, 256, 4, 15, 256, 4, 4, jmg.JMG_F64, 256, None) == -6
+    assert f(4, 1, 1, 256, 4, 16, 256, 3, 4, jmg.JMG_F64, 256, None) == -8
+    assert f(4, 2, 1, 256, 4, 16, 256, 4, 4, jmg.JMG_F64, 256, None) == -9
+    assert f(4, 1, 1, 256, 4, 16, 256, 4, 4, 9, 256, None) == -10
+    assert f(4, 1, 1, 256, 4, 16, 256, 4, 4, jmg.JMG_F64, None, None) == -11
+    assert f(129, 1, 1, 256, 129, 129 * 129, 256, 129, 129, jmg.JMG_F64, 256, None) == 6
