@@ -23,7 +23,7 @@
 // reduction kernel as the CUDA-core residual.
 //
 // tcgen05 kernel, 576 threads: warp 0 issues TMA loads (8 X-slice tiles per
-// 64-wide K block, then 8 A-slice tiles through a 4-stage ring), warp 1 issues
+// 64-wide K block, then 8 A-slice tiles through a 6-stage ring), warp 1 issues
 // the MMAs (M = 128, K = 16, N = up to 256: consecutive X slices of one A
 // slice in one instruction), warps 2-17 drain
 // TMEM (up to four per TMEM lane quarter, 16 columns each).  All waits are
@@ -39,7 +39,7 @@ constexpr int S = 8;        // slices per operand
 constexpr int BM = 128;     // rows per tile
 constexpr int BK = 64;      // K per block: 64 BF16 = one 128-byte swizzle row
 constexpr int WIN = 4;      // K blocks per exact accumulation window (256 values)
-constexpr int ASTAGES = 4;  // ring of A-slice tiles
+constexpr int ASTAGES = 6;  // ring of A-slice tiles
 constexpr int THREADS = 576;  // warps 0-1 producer / MMA, 2-17 epilogue (16 columns each)
 constexpr int A_TILE = BM * BK * 2;  // 16 KiB
 
