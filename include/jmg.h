@@ -12,7 +12,8 @@
  *  - Matrices are column-major: element (i, j) of A lives at A[i + j*lda].
  *  - Only the LOWER triangle of A is read.  The strict upper triangle and the
  *    padding rows n..lda-1 are never read or written.
- *  - Every pointer to matrix data is a DEVICE pointer owned by the caller; the
+ *  - Every pointer to matrix data is a DEVICE pointer owned by the caller
+ *    (jmg_posv_host alone takes host matrices and stages them in `work`); the
  *    library allocates no device memory.  Scratch space is the caller's `work`
  *    buffer, sized by jmg_workspace_size() (alignment: 256 bytes).
  *  - `stream` is a cudaStream_t passed as void*; work is queued on it in
@@ -48,7 +49,7 @@ typedef enum {
 
 typedef enum { JMG_REFINE_IR = 0, JMG_REFINE_PCG = 1, JMG_REFINE_AUTO = 2 } jmg_refine;
 
-typedef enum { JMG_OP_POTRF = 0, JMG_OP_POTRS = 1, JMG_OP_POSV = 2 } jmg_op;
+typedef enum { JMG_OP_POTRF = 0, JMG_OP_POTRS = 1, JMG_OP_POSV = 2, JMG_OP_POSV_HOST = 3 } jmg_op;
 
 enum {
   JMG_OK = 0,
@@ -100,6 +101,8 @@ typedef struct {
   double t_solve_gpu_ms; /* with opt->timing: summed CUDA-event time of the triangular   */
   int n_solve;           /*   solve pairs (L Y = R, L^T Z = Y) and their number          */
   double t_factor_gpu_ms; /* with opt->timing: CUDA-event time of the factorisations    */
+  long long h2d_bytes;    /* jmg_posv_host: bytes copied host -> device (0 otherwise)    */
+  long long d2h_bytes;    /* jmg_posv_host: bytes copied device -> host (0 otherwise)    */
 } jmg_stats;
 
 /* Fill *opt with the defaults: nb 128, NB 128, prec NATIVE, words 1, tol 1e-13,
@@ -178,6 +181,36 @@ int jmg_potrs_static(int n, int nrhs, const void* L, int lda, void* B, int ldb, 
 int jmg_posv(int n, int nrhs, void* A, int lda, void* B, int ldb, int dtype, int* info,
              const jmg_options* opt, jmg_stats* stats, void* work, size_t lwork,
              void* stream);
+
+/*
+ * posv_host -- jmg_posv on HOST buffers: the call copies lower(A) and B to the
+ * device, solves there exactly as jmg_posv does (every step in the library's
+ * kernels) and copies X back, returning once X is in host memory.  It is the
+ * whole job as a caller without device-resident data sees it.
+ *   A       host, n x n column-major, lda >= max(1, n).  The n x n block is
+ *           transferred whole (one linear copy when lda == n); its strict upper
+ *           triangle travels along but is never used.  (Skipping it would take
+ *           one copy row per column, about 1 us each on GB300: more than the
+ *           bytes it saves below n ~ 50000.)
+ *   B       host, n x nrhs, ldb >= max(1, n); read only
+ *   X       host, n x nrhs, ldx >= max(1, n); may be B itself.  Holds the
+ *           solution on JMG_OK and the last iterate on JMG_ERR_NOT_CONVERGED;
+ *           otherwise its contents are unspecified
+ *   dtype   JMG_F64 (every mode) or JMG_F32 (prec NATIVE)
+ *   info    HOST int: 0, or k > 0 when the leading minor of order k is not
+ *           positive definite (the call then returns JMG_ERR_NOT_SPD)
+ *   opt, stats  as jmg_posv; stats->h2d_bytes / d2h_bytes report the copies
+ *   work    device, jmg_workspace_size(JMG_OP_POSV_HOST, n, nrhs, dtype, opt)
+ *           bytes, 256-byte aligned: the device copies of A and B, then
+ *           jmg_posv's own workspace.  Host A, B and X are neither kept nor
+ *           registered; page-locked host memory (cudaHostAlloc,
+ *           cudaHostRegister) copies fastest.
+ * Synchronous: the call synchronises `stream` before it returns, on every
+ * path that queued work, so the host buffers may be reused at once.
+ */
+int jmg_posv_host(int n, int nrhs, const void* A, int lda, const void* B, int ldb, void* X,
+                  int ldx, int dtype, int* info, const jmg_options* opt, jmg_stats* stats,
+                  void* work, size_t lwork, void* stream);
 
 /*
  * posv_batched -- many small independent systems A_b X_b = B_b (b = 0 .. batch-1)

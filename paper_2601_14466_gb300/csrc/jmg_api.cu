@@ -586,6 +586,41 @@ __global__ void k_logdet(int n, const T* __restrict__ L, int lda, double* __rest
   if (threadIdx.x == 0) *out = 2.0 * part[0];
 }
 
+// ---------------------------------------------------------------- host-buffer posv
+// jmg_posv_host stages its operands at the front of `work`: the device copy of
+// A (leading dimension n), then that of B (leading dimension n), then the
+// device info word, then jmg_posv's own workspace.
+struct HostStage {
+  size_t off_B = 0, off_info = 0, off_posv = 0;
+};
+
+static HostStage host_stage(int n, int nrhs, size_t es) {
+  HostStage h;
+  h.off_B = round_up(es * (size_t)n * (size_t)n, 256);
+  h.off_info = h.off_B + round_up(es * (size_t)n * (size_t)std::max(nrhs, 1), 256);
+  h.off_posv = h.off_info + 256;
+  return h;
+}
+
+// One rows x cols column-major block between host and device in one copy: a
+// linear copy when the block is contiguous on both sides, else a 2-D copy.
+// The whole block moves, so a symmetric A travels with its upper triangle: a
+// copy that skips it needs one copy row per column, and on GB300 each row
+// costs about 1 us of copy-engine time, more than the bytes it saves below
+// n ~ 50000.  Adds the bytes to *bytes.
+static int copy_block(void* dst, int ldd, const void* src, int lds, int rows, int cols, size_t es,
+                      cudaMemcpyKind kind, long long* bytes, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return JMG_OK;
+  const size_t row_bytes = es * (size_t)rows;
+  if (cols == 1 || (lds == rows && ldd == rows))
+    JMG_CUDA(cudaMemcpyAsync(dst, src, row_bytes * (size_t)cols, kind, s));
+  else
+    JMG_CUDA(cudaMemcpy2DAsync(dst, es * (size_t)ldd, src, es * (size_t)lds, row_bytes,
+                               (size_t)cols, kind, s));
+  *bytes += (long long)(row_bytes * (size_t)cols);
+  return JMG_OK;
+}
+
 }  // namespace jmg
 
 using namespace jmg;
@@ -608,9 +643,13 @@ void jmg_default_options(jmg_options* o) {
 }
 
 size_t jmg_workspace_size(int op, int n, int nrhs, int dtype, const jmg_options* opt) {
-  (void)dtype;
   jmg_options o;
   opts_or_default(opt, &o);
+  if (op == JMG_OP_POSV_HOST) {
+    if (n <= 0 || (dtype != JMG_F64 && dtype != JMG_F32)) return 0;
+    const size_t es = dtype == JMG_F32 ? sizeof(float) : sizeof(double);
+    return host_stage(n, nrhs, es).off_posv + jmg_workspace_size(JMG_OP_POSV, n, nrhs, dtype, &o);
+  }
   if (op == JMG_OP_POSV && o.prec != JMG_PREC_NATIVE && n > 0)
     return plan_posv_mixed(n, nrhs, o).total;
   if (op == JMG_OP_POSV || op == JMG_OP_POTRS) return plain_solve_bytes(n, nrhs);
@@ -707,11 +746,77 @@ int jmg_posv(int n, int nrhs, void* A, int lda, void* B, int ldb, int dtype, int
   if (o.prec != JMG_PREC_BF16 && o.prec != JMG_PREC_FP16 && o.prec != JMG_PREC_FP8)
     return JMG_ERR_UNSUPPORTED;
   if (o.prec == JMG_PREC_FP8 && o.nb != 128) return -9;
-  if (nrhs == 0) return JMG_OK;
+  if (nrhs == 0) {
+    JMG_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
+    return JMG_OK;
+  }
   size_t need = plan_posv_mixed(n, nrhs, o).total;
   if (!work || lwork < need) return JMG_ERR_WORKSPACE;
   if (reinterpret_cast<uintptr_t>(work) & 255) return JMG_ERR_ALIGN;
   return posv_mixed(n, nrhs, (const double*)A, lda, (double*)B, ldb, info, o, stats, work, s);
+}
+
+int jmg_posv_host(int n, int nrhs, const void* A, int lda, const void* B, int ldb, void* X,
+                  int ldx, int dtype, int* info, const jmg_options* opt, jmg_stats* stats,
+                  void* work, size_t lwork, void* stream) {
+  if (n < 0) return -1;
+  if (nrhs < 0) return -2;
+  if (lda < std::max(1, n)) return -4;
+  if (ldb < std::max(1, n)) return -6;
+  if (ldx < std::max(1, n)) return -8;
+  if (dtype != JMG_F64 && dtype != JMG_F32) return -9;
+  if (!info) return -10;
+  jmg_options o;
+  opts_or_default(opt, &o);
+  if (o.nb != 64 && o.nb != 128) return -11;
+  if (o.prec == JMG_PREC_FP8 && o.nb != 128) return -11;
+  if (stats) *stats = jmg_stats{};
+  *info = 0;
+  if (n == 0) return JMG_OK;
+  if (!A) return -3;
+  if (nrhs > 0 && !B) return -5;
+  if (nrhs > 0 && !X) return -7;
+  if (o.prec != JMG_PREC_NATIVE && dtype == JMG_F32) return JMG_ERR_UNSUPPORTED;
+  if (o.prec != JMG_PREC_NATIVE && o.prec != JMG_PREC_BF16 && o.prec != JMG_PREC_FP16 &&
+      o.prec != JMG_PREC_FP8)
+    return JMG_ERR_UNSUPPORTED;
+  const size_t es = dtype == JMG_F32 ? sizeof(float) : sizeof(double);
+  const HostStage h = host_stage(n, nrhs, es);
+  const size_t need = jmg_workspace_size(JMG_OP_POSV_HOST, n, nrhs, dtype, &o);
+  if (!work || lwork < need) return JMG_ERR_WORKSPACE;
+  if (reinterpret_cast<uintptr_t>(work) & 255) return JMG_ERR_ALIGN;
+  char* w = static_cast<char*>(work);
+  char* Ad = w;
+  char* Bd = w + h.off_B;
+  int* info_d = reinterpret_cast<int*>(w + h.off_info);
+  cudaStream_t s = (cudaStream_t)stream;
+  long long h2d = 0, d2h = 0;
+  // From the first queued copy on, every path synchronises before it returns:
+  // the copies read and write the caller's host buffers.
+  int st = copy_block(Ad, n, A, lda, n, n, es, cudaMemcpyHostToDevice, &h2d, s);
+  if (st == JMG_OK) st = copy_block(Bd, n, B, ldb, n, nrhs, es, cudaMemcpyHostToDevice, &h2d, s);
+  if (st == JMG_OK)
+    st = jmg_posv(n, nrhs, Ad, n, Bd, n, dtype, info_d, &o, stats, w + h.off_posv,
+                  lwork - h.off_posv, stream);
+  int hinfo = 0;
+  if (st == JMG_OK || st == JMG_ERR_NOT_CONVERGED || st == JMG_ERR_NOT_SPD) {
+    if (copy_block(X, ldx, Bd, n, n, nrhs, es, cudaMemcpyDeviceToHost, &d2h, s) != JMG_OK)
+      st = JMG_ERR_CUDA;
+    if (cudaMemcpyAsync(&hinfo, info_d, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      st = JMG_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess && st == JMG_OK) st = JMG_ERR_CUDA;
+  if (st < 0) st = JMG_ERR_CUDA;  // the arguments were checked above: cannot happen
+  *info = hinfo;
+  if (st == JMG_OK && hinfo > 0) st = JMG_ERR_NOT_SPD;
+  if (st == JMG_OK && hinfo < 0) st = JMG_ERR_TIMEOUT;
+  if (stats) {
+    stats->status = st;
+    stats->info = hinfo;
+    stats->h2d_bytes = h2d;
+    stats->d2h_bytes = d2h;
+  }
+  return st;
 }
 
 int jmg_posv_batched(int n, int nrhs, int batch, void* A, int lda, long long strideA, void* B,

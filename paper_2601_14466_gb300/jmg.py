@@ -29,7 +29,7 @@ _lib = None
 JMG_F64, JMG_F32 = 0, 1
 PREC = {"fp64": 0, "native": 0, "bf16": 1, "fp16": 2, "fp8": 3}
 REFINE = {"ir": 0, "pcg": 1, "auto": 2}
-OP_POTRF, OP_POTRS, OP_POSV = 0, 1, 2
+OP_POTRF, OP_POTRS, OP_POSV, OP_POSV_HOST = 0, 1, 2, 3
 
 STATUS = {0: "ok", 1: "CUDA error", 2: "workspace too small", 3: "matrix is not positive definite",
           4: "refinement did not reach the tolerance", 5: "device-side wait timed out",
@@ -59,7 +59,8 @@ class Stats(ctypes.Structure):
                 ("t_refine_ms", ctypes.c_double), ("t_resid_gpu_ms", ctypes.c_double),
                 ("n_resid", ctypes.c_int), ("n_hist", ctypes.c_int),
                 ("eta_hist", ctypes.c_double * 32), ("t_solve_gpu_ms", ctypes.c_double),
-                ("n_solve", ctypes.c_int), ("t_factor_gpu_ms", ctypes.c_double)]
+                ("n_solve", ctypes.c_int), ("t_factor_gpu_ms", ctypes.c_double),
+                ("h2d_bytes", ctypes.c_longlong), ("d2h_bytes", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -77,6 +78,8 @@ _SIGS = {
     "jmg_potrs_static": (_I, [_I, _I, _P, _I, _P, _I, _I, _P]),
     "jmg_posv": (_I, [_I, _I, _P, _I, _P, _I, _I, _P, ctypes.POINTER(Options),
                       ctypes.POINTER(Stats), _P, _SZ, _P]),
+    "jmg_posv_host": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _I, ctypes.POINTER(_I),
+                           ctypes.POINTER(Options), ctypes.POINTER(Stats), _P, _SZ, _P]),
     "jmg_logdet": (_I, [_I, _P, _I, _I, _P, _P]),
     "jmg_status_string": (ctypes.c_char_p, [_I]),
     "jmg_sym_grad": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P]),
@@ -169,12 +172,14 @@ def default_options(**kw) -> Options:
     return o
 
 
-def workspace_size(op: int, n: int, nrhs: int, opts: Options | None = None) -> int:
-    return int(load().jmg_workspace_size(op, n, nrhs, JMG_F64, ctypes.byref(opts) if opts else None))
+def workspace_size(op: int, n: int, nrhs: int, opts: Options | None = None,
+                   dtype: int = JMG_F64) -> int:
+    return int(load().jmg_workspace_size(op, n, nrhs, dtype, ctypes.byref(opts) if opts else None))
 
 
-def workspace(op: int, n: int, nrhs: int, opts: Options | None, device) -> torch.Tensor:
-    nbytes = workspace_size(op, n, nrhs, opts)
+def workspace(op: int, n: int, nrhs: int, opts: Options | None, device,
+              dtype: int = JMG_F64) -> torch.Tensor:
+    nbytes = workspace_size(op, n, nrhs, opts, dtype)
     return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
 
 
@@ -240,6 +245,25 @@ class SolveInfo:
     t_solve_gpu_ms: float = 0.0
     n_solve: int = 0
     t_factor_gpu_ms: float = 0.0
+    h2d_bytes: int = 0
+    d2h_bytes: int = 0
+
+
+def _solve_info(stats: Stats) -> SolveInfo:
+    return SolveInfo(stats.status, stats.info, stats.iters, stats.bwd_err, stats.shift,
+                     stats.words_used, stats.factor_tries, stats.anorm, stats.t_factor_ms,
+                     stats.t_solve_ms, stats.t_refine_ms, stats.refine_used,
+                     stats.t_resid_gpu_ms, stats.n_resid,
+                     tuple(stats.eta_hist[i] for i in range(min(stats.n_hist, 32))),
+                     stats.t_solve_gpu_ms, stats.n_solve, stats.t_factor_gpu_ms,
+                     stats.h2d_bytes, stats.d2h_bytes)
+
+
+def _options(prec, words, nb, tol, maxit, refine, shift_retry, timing, reuse_factor, resid):
+    return default_options(nb=nb, prec=prec, words=words, tol=tol, maxit=maxit, refine=refine,
+                           shift_retry=int(shift_retry), timing=int(timing),
+                           reuse_factor=int(reuse_factor),
+                           resid={"auto": 0, "fp64": 1, "split": 2}[resid])
 
 
 def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1, nb: int = 128,
@@ -264,10 +288,7 @@ def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1
         B = B.reshape(-1, 1)
     n, nrhs = A.shape[0], B.shape[1]
     X = colmajor_copy(B)
-    o = default_options(nb=nb, prec=prec, words=words, tol=tol, maxit=maxit, refine=refine,
-                        shift_retry=int(shift_retry), timing=int(timing),
-                        reuse_factor=int(reuse_factor),
-                        resid={"auto": 0, "fp64": 1, "split": 2}[resid])
+    o = _options(prec, words, nb, tol, maxit, refine, shift_retry, timing, reuse_factor, resid)
     Aw = A if (overwrite_a or o.prec != 0) else colmajor_copy(A)
     pa, lda = _colmajor(Aw, "A")
     px, ldx = _colmajor(X, "B")
@@ -284,14 +305,65 @@ def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1
         if check and (st != 0 or info_h != 0):
             raise JmgError(st if st else 3, "jmg_posv(info=%d)" % info_h)
     else:
-        si = SolveInfo(stats.status, stats.info, stats.iters, stats.bwd_err, stats.shift,
-                       stats.words_used, stats.factor_tries, stats.anorm, stats.t_factor_ms,
-                       stats.t_solve_ms, stats.t_refine_ms, stats.refine_used,
-                       stats.t_resid_gpu_ms, stats.n_resid,
-                       tuple(stats.eta_hist[i] for i in range(min(stats.n_hist, 32))),
-                       stats.t_solve_gpu_ms, stats.n_solve, stats.t_factor_gpu_ms)
+        si = _solve_info(stats)
         if check and st != 0:
             raise JmgError(st, "jmg_posv")
+    return (X[:, 0] if squeeze else X), si
+
+
+def posv_host(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1,
+              nb: int = 128, tol: float = 1e-13, maxit: int = 300, refine: str = "auto",
+              shift_retry: bool = True, out: torch.Tensor | None = None,
+              work: torch.Tensor | None = None, check: bool = True, timing: bool = False,
+              reuse_factor: bool = False, resid: str = "auto", device=None):
+    """Solve A X = B with A and B in HOST memory (CPU tensors, column-major;
+    page-locked ones copy fastest) through ``jmg_posv_host``: A and B go
+    to the GPU, the solve runs there in the library's kernels (modes as
+    :func:`posv`), and X comes back.  Returns ``(X, SolveInfo)``: X is ``out``
+    when given (a column-major CPU tensor, which may be B itself), else a new
+    one; ``work`` is a device byte tensor of at least
+    ``workspace_size(OP_POSV_HOST, ...)`` bytes.  Blocks until X is on the host."""
+    if not torch.cuda.is_available():
+        raise RuntimeError("jmg.posv_host: no CUDA device (the solve has no CPU path)")
+    for t, name in ((A, "A"), (B, "B")):
+        if t.is_cuda:
+            raise ValueError("posv_host: %s must be a host (CPU) tensor; use posv for device data"
+                             % name)
+    if A.dtype != B.dtype:
+        raise TypeError("posv_host: A and B must have the same dtype")
+    dt = _dtype_code(A)
+    if dt == JMG_F32 and prec != "fp64":
+        raise TypeError("posv_host: the mixed modes refine FP64 data; float32 takes prec='fp64'")
+    squeeze = B.dim() == 1
+    if squeeze:
+        B = B.reshape(-1, 1)
+    if A.dim() != 2 or A.shape[0] != A.shape[1] or B.dim() != 2 or B.shape[0] != A.shape[0]:
+        raise ValueError("posv_host: A (n, n) and B (n, nrhs) or (n,)")
+    n, nrhs = A.shape[0], B.shape[1]
+    if out is None:
+        X = torch.empty((nrhs, n), dtype=B.dtype, pin_memory=B.is_pinned()).t()
+    else:
+        X = out.reshape(-1, 1) if out.dim() == 1 else out
+        if X.is_cuda or X.dtype != B.dtype or tuple(X.shape) != (n, nrhs):
+            raise ValueError("posv_host: out must be a host tensor shaped and typed like B")
+    pa, lda = _colmajor(A, "A")
+    pb, ldb = _colmajor(B, "B")
+    px, ldx = _colmajor(X, "out")
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None \
+        else torch.device(device)
+    o = _options(prec, words, nb, tol, maxit, refine, shift_retry, timing, reuse_factor, resid)
+    if work is None:
+        work = workspace(OP_POSV_HOST, n, nrhs, o, dev, dt)
+    info = ctypes.c_int(0)
+    stats = Stats()
+    with torch.cuda.device(dev):
+        st = load().jmg_posv_host(n, nrhs, pa, lda, pb, ldb, px, ldx, dt, ctypes.byref(info),
+                                  ctypes.byref(o), ctypes.byref(stats), work.data_ptr(),
+                                  work.numel(), _stream(dev))
+    si = _solve_info(stats)
+    si.status, si.info = st, info.value
+    if check and st != 0:
+        raise JmgError(st, "jmg_posv_host(info=%d)" % info.value)
     return (X[:, 0] if squeeze else X), si
 
 

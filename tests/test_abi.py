@@ -94,9 +94,10 @@ def test_struct_layouts_match_the_header(tmp_path):
     # the ctypes mirrors of jmg_options / jmg_stats must have the C layout
     src = tmp_path / "sizes.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "jmg.h"\n'
-                   'int main(void) { printf("%zu %zu %zu %zu %zu\\n", sizeof(jmg_options), '
-                   'sizeof(jmg_stats), offsetof(jmg_stats, eta_hist), '
-                   'offsetof(jmg_stats, n_solve), offsetof(jmg_stats, t_factor_gpu_ms)); '
+                   'int main(void) { printf("%zu %zu %zu %zu %zu %zu %zu\\n", '
+                   'sizeof(jmg_options), sizeof(jmg_stats), offsetof(jmg_stats, eta_hist), '
+                   'offsetof(jmg_stats, n_solve), offsetof(jmg_stats, t_factor_gpu_ms), '
+                   'offsetof(jmg_stats, h2d_bytes), offsetof(jmg_stats, d2h_bytes)); '
                    'return 0; }\n')
     exe = tmp_path / "sizes"
     import subprocess
@@ -105,7 +106,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
                                           text=True).stdout.split()]
     want = [ctypes.sizeof(jmg.Options), ctypes.sizeof(jmg.Stats), jmg.Stats.eta_hist.offset,
-            jmg.Stats.n_solve.offset, jmg.Stats.t_factor_gpu_ms.offset]
+            jmg.Stats.n_solve.offset, jmg.Stats.t_factor_gpu_ms.offset,
+            jmg.Stats.h2d_bytes.offset, jmg.Stats.d2h_bytes.offset]
     assert got == want
 
 
@@ -123,3 +125,66 @@ def test_posv_batched_argument_checks():
     assert f(4, 1, 1, 256, 4, 16, 256, 4, 4, 9, 256, None) == -10
     assert f(4, 1, 1, 256, 4, 16, 256, 4, 4, jmg.JMG_F64, None, None) == -11
     assert f(129, 1, 1, 256, 129, 129 * 129, 256, 129, 129, jmg.JMG_F64, 256, None) == 6
+
+
+def test_posv_host_argument_checks():
+    lib = jmg.load()
+    f = lib.jmg_posv_host
+    info = ctypes.c_int(-7)
+    h = ctypes.c_void_p(4096)  # never dereferenced: the checks fire first
+    # (n, nrhs, A, lda, B, ldb, X, ldx, dtype, info, opt, stats, work, lwork, stream)
+    assert f(-1, 1, h, 1, h, 1, h, 1, jmg.JMG_F64, ctypes.byref(info), None, None, None, 0,
+             None) == -1
+    assert f(4, -1, h, 4, h, 4, h, 4, jmg.JMG_F64, ctypes.byref(info), None, None, None, 0,
+             None) == -2
+    assert f(4, 1, h, 3, h, 4, h, 4, jmg.JMG_F64, ctypes.byref(info), None, None, None, 0,
+             None) == -4
+    assert f(4, 1, h, 4, h, 3, h, 4, jmg.JMG_F64, ctypes.byref(info), None, None, None, 0,
+             None) == -6
+    assert f(4, 1, h, 4, h, 4, h, 3, jmg.JMG_F64, ctypes.byref(info), None, None, None, 0,
+             None) == -8
+    assert f(4, 1, h, 4, h, 4, h, 4, 5, ctypes.byref(info), None, None, None, 0, None) == -9
+    assert f(4, 1, h, 4, h, 4, h, 4, jmg.JMG_F64, None, None, None, None, 0, None) == -10
+    o = jmg.default_options(nb=96)
+    assert f(4, 1, h, 4, h, 4, h, 4, jmg.JMG_F64, ctypes.byref(info), ctypes.byref(o), None,
+             None, 0, None) == -11
+    o = jmg.default_options(prec="fp8", nb=64)
+    assert f(4, 1, h, 4, h, 4, h, 4, jmg.JMG_F64, ctypes.byref(info), ctypes.byref(o), None,
+             None, 0, None) == -11
+    # n == 0: nothing to do, info cleared, no device touched
+    assert f(0, 3, None, 1, None, 1, None, 1, jmg.JMG_F64, ctypes.byref(info), None, None,
+             None, 0, None) == 0 and info.value == 0
+    assert f(4, 1, None, 4, h, 4, h, 4, jmg.JMG_F64, ctypes.byref(info), None, None, None, 0,
+             None) == -3
+    assert f(4, 1, h, 4, None, 4, h, 4, jmg.JMG_F64, ctypes.byref(info), None, None, None, 0,
+             None) == -5
+    assert f(4, 1, h, 4, h, 4, None, 4, jmg.JMG_F64, ctypes.byref(info), None, None, None, 0,
+             None) == -7
+    # mixed modes refine FP64 data only
+    o = jmg.default_options(prec="bf16")
+    assert f(4, 1, h, 4, h, 4, h, 4, jmg.JMG_F32, ctypes.byref(info), ctypes.byref(o), None,
+             None, 0, None) == 6  # JMG_ERR_UNSUPPORTED
+    # the staging buffers must fit: checked before any copy is queued
+    assert f(4, 1, h, 4, h, 4, h, 4, jmg.JMG_F64, ctypes.byref(info), None, None, None, 0,
+             None) == 2  # JMG_ERR_WORKSPACE
+    need = jmg.workspace_size(jmg.OP_POSV_HOST, 4, 1)
+    assert f(4, 1, h, 4, h, 4, h, 4, jmg.JMG_F64, ctypes.byref(info), None, None,
+             ctypes.c_void_p(4096 + 16), need, None) == 7  # JMG_ERR_ALIGN
+
+
+def test_posv_host_workspace_stages_a_and_b():
+    for prec, words in (("fp64", 1), ("bf16", 2), ("fp8", 1)):
+        o = jmg.default_options(prec=prec, words=words)
+        for n, nrhs in ((1, 1), (257, 3), (4096, 64)):
+            for dt, es in ((jmg.JMG_F64, 8), (jmg.JMG_F32, 4)):
+                if dt == jmg.JMG_F32 and prec != "fp64":
+                    continue
+                inner = jmg.workspace_size(jmg.OP_POSV, n, nrhs, o, dt)
+                host = jmg.workspace_size(jmg.OP_POSV_HOST, n, nrhs, o, dt)
+                stage = host - inner
+                # the device copies of A (n x n) and B (n x nrhs), each rounded to
+                # 256 bytes, and one 256-byte slot for the device info word
+                r = lambda b: (b + 255) // 256 * 256
+                assert stage == r(es * n * n) + r(es * n * nrhs) + 256
+    assert jmg.workspace_size(jmg.OP_POSV_HOST, 0, 4) == 0
+    assert jmg.workspace_size(jmg.OP_POSV_HOST, 10, 4, None, 7) == 0
