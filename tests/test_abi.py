@@ -188,3 +188,19 @@ def test_posv_host_workspace_stages_a_and_b():
                 assert stage == r(es * n * n) + r(es * n * nrhs) + 256
     assert jmg.workspace_size(jmg.OP_POSV_HOST, 0, 4) == 0
     assert jmg.workspace_size(jmg.OP_POSV_HOST, 10, 4, None, 7) == 0
+
+
+def test_plain_c_caller_links_and_runs(tmp_path):
+    # the headers compile as C11 and a C program linked against libjmg.so runs
+    # the host-side checks of the ABI (no GPU needed)
+    import subprocess
+
+    lib = jmg.load()
+    libdir = os.path.dirname(jmg.lib_path())
+    exe = tmp_path / "abi_from_c"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c", "abi_from_c.c"), "-o", str(exe),
+                    "-L" + libdir, "-ljmg", "-Wl,-rpath," + libdir], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
+    assert lib is not None
