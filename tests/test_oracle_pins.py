@@ -178,8 +178,12 @@ def pin_bwd_err_formula(o):
     A = np.tril(rng.integers(-9, 10, (n, n)).astype(float))
     A = A + np.diag(np.full(n, 40.0))
     X = rng.integers(-5, 6, (n, 3)).astype(float)
-    B = _full(A) @ X + rng.integers(-3, 4, (n, 3)).astype(float)  # exact integers
+    E = rng.integers(-3, 4, (n, 3)).astype(float)
+    E[:, 0] = 0.0  # column 0 solved exactly: the maximum must come from another column
+    E[0, 2] = 5.0
+    B = _full(A) @ X + E  # exact integers
     eta, per = o.bwd_err(A, X, B)
+    assert per[0] == 0.0 and eta > 0.0
     Af = _full(A)
     anorm = np.abs(Af).sum(axis=1).max()
     assert o.norm_inf(A) == anorm
@@ -309,6 +313,23 @@ MUTANTS = {
                        "(void)t;"),
     "ge_back_index": ("s -= M[(size_t)j * n + i] * AT(B, j, c, ldb);",
                       "s -= M[(size_t)i * n + j] * AT(B, j, c, ldb);"),
+    "forward_no_divide": ("double yj = b[j] / AT(L, j, j, lda);", "double yj = b[j];"),
+    "update_skips_next_col": ("for (int k = j + 1; k < n; ++k) {\n      double lkj",
+                              "for (int k = j + 2; k < n; ++k) {\n      double lkj"),
+    "twoprod_sign": ("*e = fma(a, b, -x);", "*e = fma(a, b, x);"),
+    "resid_sign": ("two_prod(-sym_at(A, lda, i, j), AT(X, j, c, ldx), &p, &ep);",
+                   "two_prod(sym_at(A, lda, i, j), AT(X, j, c, ldx), &p, &ep);"),
+    "resid_lower_row_only": ("      for (int j = 0; j < n; ++j) {\n        double p, ep, es;",
+                             "      for (int j = 0; j <= i; ++j) {\n        double p, ep, es;"),
+    "norm_lower_row_only": ("for (int j = 0; j < n; ++j) s += fabs(sym_at(A, lda, i, j));",
+                            "for (int j = 0; j <= i; ++j) s += fabs(sym_at(A, lda, i, j));"),
+    "norm_sums_rows": ("if (s > best || isnan(s)) best = s;", "best += s;"),
+    "bwd_first_column_only": ("if (e > worst || isnan(e)) worst = e;", "if (c == 0) worst = e;"),
+    "bwd_x_from_b": ("xn = nan_max(xn, fabs(AT(X, i, c, ldx)));",
+                     "xn = nan_max(xn, fabs(AT(B, i, c, ldb)));"),
+    "grad_uses_b": ("Bbar[(size_t)c * n + i] = AT(Xbar, i, c, ldxb);",
+                    "Bbar[(size_t)c * n + i] = AT(B, i, c, ldb);"),
+    "logdet_no_log": ("s += log(AT(L, i, i, lda));", "s += AT(L, i, i, lda);"),
 }
 
 
