@@ -3,11 +3,19 @@
 mixed precision + FP64 refinement vs plain FP64, on one GB300.
 
 One step = one posv call (factor + solves + refinement) on the workload's
-synthetic matrix, resident in HBM (A is 2.1 GB at n = 16384, larger than the
-129 MB L2, so no flush is needed between steps).  TFLOP/s uses the nominal
-count n^3/3 + 2 n^2 nrhs.  Prints ONE JSON line.
+synthetic matrix, resident in HBM.  The default workload is the largest
+single-GPU configuration: n = 65536, nrhs = 32, A = M M^T/n + 1e-2 I with FP8
+e4m3 trailing updates (per-tile power-of-two scales) and FP64 refinement,
+against the plain FP64 path on the same system.  A (34 GB) is far larger than
+the 129 MB L2, so no flush is needed between steps.  TFLOP/s uses the nominal
+count n^3/3 + 2 n^2 nrhs.  Every returned X is certified on the host by the
+CPU oracle's Dot2 backward error.  Prints ONE JSON line; `extra_configs` holds
+one timed solve of each other configuration (n = 1024; n = 32768 at
+kappa = 1e2 .. 1e8 with BF16 and FP16 words; the autograd workload at
+n = 8192; the paper's diag(1..N)).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c1|c3|c4]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c4|c2|...]
+                  [--extra c1,c3,c5,c6|none]
   python bench.py --impl reference ...   (the CPU oracle, timed on host cores)
 
 With N > 1 (torchrun) every rank runs an independent replica on its own GPU
@@ -23,7 +31,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -32,7 +39,7 @@ sys.path.insert(0, ROOT)
 METRIC = ("posv TFLOP/s & time-to-solution at backward err ≤1e-13: mixed+IR vs FP64, "
           "1×GB300")
 
-# workload -> (n, nrhs, matrix kind, kappa or shift, default precision ladder)
+# workload -> (n, nrhs, matrix kind, kappa or shift, precision, words)
 WORKLOADS = {
     "c1": dict(n=1024, nrhs=1, kind="gram", param=1.0, prec="bf16", words=1,
                desc="posv n=1024 nrhs=1, A = M M^T/n + I"),
@@ -41,23 +48,21 @@ WORKLOADS = {
     "c3": dict(n=32768, nrhs=16, kind="qlam", param=1e4, prec="fp16", words=2,
                desc="posv n=32768 nrhs=16, A = Q diag(logspace[1,kappa]) Q^T"),
     "c4": dict(n=65536, nrhs=32, kind="gram32", param=1e-2, prec="fp8", words=1,
-               desc="posv n=65536 nrhs=32, A = M M^T/n + 1e-2 I (product formed in FP32)"),
-    "c6": dict(n=16384, nrhs=1, kind="diag", param=0.0, prec="bf16", words=1,
-               desc="posv n=16384 nrhs=1, the paper's A = diag(1..N), b = ones (x_i = 1/i)"),
+               desc="posv n=65536 nrhs=32, A = M M^T/n + 1e-2 I (product formed in FP32), "
+                    "FP8 e4m3 trailing updates with per-128x128-tile power-of-two scales"),
     "c5": dict(n=8192, nrhs=16, kind="gram", param=1.0, prec="bf16", words=2,
                desc="autograd forward+backward n=8192 nrhs=16, A = M M^T/n + I, B ~ N(0,1), "
                     "loss 0.5||X||^2", rhs="normal"),
+    "c6": dict(n=16384, nrhs=1, kind="diag", param=0.0, prec="bf16", words=1,
+               desc="posv n=16384 nrhs=1, the paper's A = diag(1..N), b = ones (x_i = 1/i)"),
 }
 
+# The n = 32768 condition-number ladder: for each kappa, the split words of the
+# BF16 and of the FP16 tensor-core factor (more words as kappa grows).
+C3_LADDER = [(1e2, {"bf16": 1, "fp16": 1}), (1e4, {"bf16": 2, "fp16": 2}),
+             (1e6, {"bf16": 3, "fp16": 2}), (1e8, {"bf16": 3, "fp16": 2})]
+
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
-
-# DRAM bytes (read + write) of one k_trsv_persist<float> launch, from one ncu
-# capture (profiles/k_trsv_persist_n16384_nrhs64.md); None where not captured.
-_SOLVE_TRAFFIC = {(16384, 64): 542343680 + 5179136}
-
-
-def SOLVE_TRAFFIC_BYTES(n, nrhs):
-    return _SOLVE_TRAFFIC.get((n, nrhs))
 
 
 def nominal_flops(n, nrhs):
@@ -87,6 +92,10 @@ def load_peaks():
             return json.load(f)
     except Exception:
         return {}
+
+
+def log(msg):
+    print("[bench %s] %s" % (time.strftime("%H:%M:%S"), msg), file=sys.stderr, flush=True)
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -146,7 +155,9 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- inputs
-def make_inputs(w, device, seed=0):
+def make_inputs(w, device, seed=0, Q=None):
+    """(A, X_true or None, B) on `device`; A symmetric (row- and column-major
+    forms coincide).  Q: an orthogonal factor to reuse for the Q-lambda kind."""
     import torch
 
     from paper_2601_14466_gb300 import inputs
@@ -158,7 +169,8 @@ def make_inputs(w, device, seed=0):
         torch.cuda.synchronize()
         return A, Xt, B
     if w["kind"] == "qlam":
-        A = inputs.q_lambda(n, w["param"], seed=seed, device=device)
+        A = inputs.from_q(Q, w["param"]) if Q is not None else \
+            inputs.q_lambda(n, w["param"], seed=seed, device=device)
     else:
         A = inputs.gram_shift(n, w["param"], seed=seed, device=device,
                               fp32_product=(w["kind"] == "gram32"))
@@ -172,43 +184,82 @@ def make_inputs(w, device, seed=0):
     return A, Xt, B
 
 
-# ----------------------------------------------------------------------------- CPU oracle leg
-def cpu_oracle_sample(w, target_s=12.0):
-    """Time the oracle (as it stands) on a bounded sample of the workload: the
-    same matrix construction at a reduced n, nrhs unchanged."""
+def host_f(t):
+    """A device (n x m) tensor as a column-major float64 NumPy array."""
     import numpy as np
 
+    return np.asfortranarray(t.detach().double().cpu().numpy())
+
+
+def certify(A_host, X, B):
+    """The CPU oracle's normwise backward error of X (Dot2 residual), max over
+    the columns; A_host: the symmetric matrix as a NumPy array (either order)."""
     import oracle
+
+    Af = A_host if A_host.flags.f_contiguous else A_host.T  # symmetric: same matrix
+    eta, _ = oracle.bwd_err_rows(Af, host_f(X), host_f(B))
+    return eta
+
+
+# ----------------------------------------------------------------------------- CPU oracle leg
+def _oracle_sample_inputs(w, n_s):
+    import numpy as np
+
     from paper_2601_14466_gb300 import inputs
 
-    n_s = min(w["n"], 3072)
     nrhs = w["nrhs"]
     if w["kind"] == "diag":
         A, B = (np.asfortranarray(t.numpy()) for t in inputs.diag_workload(n_s))
+        return A, B
+    if w["kind"] == "qlam":
+        A = inputs.q_lambda(n_s, w["param"], seed=11).numpy()
     else:
-        if w["kind"] == "qlam":
-            A = inputs.q_lambda(n_s, w["param"], seed=11).numpy()
-        else:
-            A = inputs.gram_shift(n_s, w["param"], seed=11).numpy()  # same construction, FP64
-        X = inputs.uniform(n_s, nrhs, seed=12).numpy()
-        B = np.asfortranarray(A @ X)
+        A = inputs.gram_shift(n_s, w["param"], seed=11).numpy()  # same construction, FP64
+    X = inputs.uniform(n_s, nrhs, seed=12).numpy()
+    return A, np.asfortranarray(A @ X)
+
+
+def oracle_sample_n(w):
+    # one solve of the sample takes about a second on 16 Grace cores
+    return min(w["n"], 4096)
+
+
+def cpu_oracle_timed(w, steps, warmup):
+    """Time the oracle (as it stands) on `warmup` + `steps` solves of a bounded
+    sample of the workload: the same construction at a reduced n, nrhs
+    unchanged.  Returns the per-solve times of the timed solves."""
+    import oracle
+
+    n_s = oracle_sample_n(w)
+    A, B = _oracle_sample_inputs(w, n_s)
     oracle.build()
-    reps, t_tot = 0, 0.0
-    while True:
+    times = []
+    for k in range(warmup + steps):
         t0 = time.perf_counter()
-        Xo, info = oracle.posv(A, B)
-        t_tot += time.perf_counter() - t0
-        reps += 1
-        if t_tot >= target_s * 0.5 or reps >= 3:
-            break
-    t = t_tot / reps
-    tf = nominal_flops(n_s, nrhs) / t / 1e12
-    return {"value": tf, "unit": "TFLOP/s", "cores": oracle.threads(), "kind": "oracle",
-            "sample": "oracle posv at n=%d nrhs=%d (same construction), %d run(s), %.2f s each"
-                      % (n_s, nrhs, reps, t), "seconds_per_solve": t}
+        _, info = oracle.posv(A, B)
+        dt = time.perf_counter() - t0
+        if info != 0:
+            raise RuntimeError("oracle posv failed on the sample (info=%d)" % info)
+        if k >= warmup:
+            times.append(dt)
+    return n_s, times
 
 
-# ----------------------------------------------------------------------------- main GPU arm
+def cpu_baseline(w, steps=2):
+    import oracle
+
+    n_s, times = cpu_oracle_timed(w, steps, 0)
+    t = statistics.mean(times)
+    F = nominal_flops(n_s, w["nrhs"])
+    return {"value": F / t / 1e12, "unit": "TFLOP/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": "oracle posv at n=%d nrhs=%d (same construction, %d timed solves, "
+                      "%.3f s each); at the workload's n=%d the same rate would take %.0f s "
+                      "per solve (n^3 extrapolation, not run)"
+                      % (n_s, w["nrhs"], len(times), t, w["n"],
+                         t * nominal_flops(w["n"], w["nrhs"]) / F)}
+
+
+# ----------------------------------------------------------------------------- GPU helpers
 def _device():
     import torch
 
@@ -243,7 +294,112 @@ def _cw_bwd_err(jmg, torch, A, Acm, X, B):
         return None
 
 
-def run_ours(args, w, rank, world):
+def _timed(stream, fn):
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def _fp64_posv(jmg, A, B, stream, steps, warmup=0, nb=128):
+    """Plain FP64 posv on a scratch copy of A (restored before every step,
+    outside the timed region); returns (ms per timed step, X)."""
+    import torch
+
+    Awork = torch.empty_like(A)
+    ms, X = [], None
+    for k in range(warmup + steps):
+        Awork.copy_(A)
+        dt, (X, _) = _timed(stream, lambda: jmg.posv(Awork.t(), B, prec="fp64", overwrite_a=True,
+                                                     check=False, nb=nb))
+        if k >= warmup:
+            ms.append(dt)
+    del Awork
+    return ms, X
+
+
+def _roofline_objects(n, nrhs, prec, words, infos, steps_ms, peaks, resid_mode):
+    """Per-launch rooflines of the solve and the residual product, from the
+    library's CUDA events inside the timed steps, and the factorisation's
+    tensor-core rate.  Returns (dominant, others)."""
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
+    src = "of measured (MEASURED_PEAKS.json)" if peaks else "of fallback"
+    n_sol = sum(si.n_solve for si in infos)
+    t_sol = sum(si.t_solve_gpu_ms for si in infos)
+    n_res = sum(si.n_resid for si in infos)
+    t_res = sum(si.t_resid_gpu_ms for si in infos)
+    t_fac = sum(si.t_factor_gpu_ms for si in infos)
+    total_ms = steps_ms * len(infos)
+    objs = {}
+    if n_sol:
+        # one triangular solve with the FP32 factor: the lower triangle of L read
+        # once, the n x nrhs block read and written once
+        sol_bytes = n * (n + 1) / 2 * 4 + 2 * n * nrhs * 4
+        launch_ms = t_sol / (2 * n_sol)
+        ach = sol_bytes / (launch_ms / 1e3) / 1e9
+        objs["solve"] = {"kernel": "triangular solve with the FP32 factor (one launch per "
+                                   "direction)",
+                         "bound": "hbm", "achieved": round(ach, 2), "peak": hbm, "unit": "GB/s",
+                         "frac": round(ach / hbm, 4), "peak_source": src,
+                         "algorithmic_bytes_per_launch": sol_bytes,
+                         "launch_ms": round(launch_ms, 4), "launches": 2 * n_sol,
+                         "share_of_step": round(t_sol / total_ms, 4)}
+    if n_res:
+        launch_ms = t_res / n_res
+        if resid_mode != "fp64":
+            # split product: 36 slice pairs of BF16 MMA work; the slices of A
+            # (8 x 2 bytes per element of the full matrix) are streamed once
+            mma = 36 * 2.0 * n * n * nrhs
+            sl_bytes = 16.0 * n * n
+            t_mma = mma / (bf16 * 1e12)
+            t_hbm = sl_bytes / (hbm * 1e9)
+            if t_hbm >= t_mma:
+                ach = sl_bytes / (launch_ms / 1e3) / 1e9
+                o = {"bound": "hbm", "achieved": round(ach, 2), "peak": hbm, "unit": "GB/s",
+                     "algorithmic_bytes_per_launch": sl_bytes}
+            else:
+                ach = mma / (launch_ms / 1e3) / 1e12
+                o = {"bound": "tensor", "achieved": round(ach, 2), "peak": bf16,
+                     "unit": "TFLOP/s", "algorithmic_flops_per_launch": mma}
+            o["kernel"] = "split FP64-accurate product A X (BF16 tensor cores, exact windows)"
+            o["fp64_equivalent_tflops"] = round(2.0 * n * n * nrhs / (launch_ms / 1e3) / 1e12, 3)
+        else:
+            ach = 2.0 * n * n * nrhs / (launch_ms / 1e3) / 1e12
+            o = {"kernel": "FP64 product A X (CUDA cores)", "bound": "alu", "achieved": round(ach, 3),
+                 "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s"}
+        o.update({"frac": round(o["achieved"] / o["peak"], 4), "peak_source": src,
+                  "launch_ms": round(launch_ms, 4), "launches": n_res,
+                  "share_of_step": round(t_res / total_ms, 4)})
+        objs["residual_product"] = o
+    if t_fac > 0:
+        pairs = {1: 1, 2: 3, 3: 6}.get(words, 1) if prec != "fp8" else 1
+        mma_f = pairs * n ** 3 / 3.0
+        pk = bf16 * (2.0 if prec == "fp8" else 1.0)  # e4m3: twice the 16-bit rate (nominal ratio)
+        fac_ms = t_fac / len(infos)
+        objs["factor"] = {"kernels": "diagonal blocks, panel solves, word split / FP8 quantise, "
+                                     "tensor-core trailing updates",
+                          "bound": "tensor", "unit": "TFLOP/s",
+                          "achieved": round(mma_f * sum(si.factor_tries for si in infos) /
+                                            len(infos) / (fac_ms / 1e3) / 1e12, 3),
+                          "peak": pk, "peak_source": src, "ms": round(fac_ms, 3),
+                          "share_of_step": round(t_fac / total_ms, 4),
+                          "note": "tensor-core MMA flops of the trailing updates (%d word pairs, "
+                                  "every factorisation of the step) over the factorisation time"
+                                  % pairs}
+        objs["factor"]["frac"] = round(objs["factor"]["achieved"] / pk, 4)
+    per_launch = {k: v for k, v in objs.items() if k != "factor"}
+    dom = max(per_launch, key=lambda k: per_launch[k]["share_of_step"]) if per_launch else None
+    return dom, objs
+
+
+# ----------------------------------------------------------------------------- main GPU arm
+def run_main(args, w, rank, world):
+    import numpy as np
     import torch
 
     from paper_2601_14466_gb300 import jmg
@@ -252,7 +408,9 @@ def run_ours(args, w, rank, world):
     jmg.load()
     n, nrhs = w["n"], w["nrhs"]
     prec, words = args.prec or w["prec"], args.words or w["words"]
+    t0 = time.time()
     A, Xt, B = make_inputs(w, dev)
+    log("inputs n=%d ready in %.1f s" % (n, time.time() - t0))
     Acm = A.t()  # symmetric: the transpose view is the column-major matrix
     kw = dict(prec=prec, words=words, nb=args.nb, maxit=args.maxit, refine=args.refine,
               resid=args.resid)
@@ -286,39 +444,31 @@ def run_ours(args, w, rank, world):
     clocks = sampler.stop()
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     t_mixed = sum(step_ms) / 1e3
+    log("mixed: %.1f ms/step" % (t_mixed * 1e3 / args.steps))
     anorm = float(jmg.norm_inf(Acm).item())
     eta = _eta(jmg, Acm, X, B, anorm)
     eta_cw = _cw_bwd_err(jmg, torch, A, Acm, X, B)
     fwd = float(((X - Xt).abs().max() / Xt.abs().max()).item()) if Xt is not None else None
 
-    # ---- plain FP64 GPU path on the same system (A restored between steps, untimed)
-    f64_steps = min(args.steps, args.fp64_steps)
-    t_f64, eta64 = None, None
+    # ---- plain FP64 GPU path on the same system
+    f64_steps = args.fp64_steps
+    t_f64, X64 = None, None
     if f64_steps > 0:
-        Awork = torch.empty_like(A)
-        Aw_cm = Awork.t()
-        f64_ms = []
-        for k in range(1 + f64_steps):
-            Awork.copy_(A)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            X64, _ = jmg.posv(Aw_cm, B, prec="fp64", overwrite_a=True, check=False, nb=args.nb)
-            e1.record(stream)
-            e1.synchronize()
-            if k > 0:
-                f64_ms.append(e0.elapsed_time(e1))
-        del Awork
+        f64_ms, X64 = _fp64_posv(jmg, A, B, stream, f64_steps, nb=args.nb)
         t_f64 = sum(f64_ms) / 1e3
-        eta64 = _eta(jmg, Acm, X64, B, anorm)
+        log("fp64: %.1f ms/step" % (t_f64 * 1e3 / f64_steps))
+
+    # ---- host copy of A: certification by the oracle, and the end-to-end leg
+    A_h = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+    A_h.copy_(A)
+    X_keep, B_keep = X.clone(), B.clone()
 
     # ---- end to end through the public API with host buffers: jmg_posv_host
     # copies A and B from page-locked host memory, solves, and copies X back,
     # all inside the timed region
-    e2e_steps = min(args.steps, args.e2e_steps)
+    e2e_steps = args.e2e_steps
     t_e2e, e2e_bytes = None, (0, 0)
     if e2e_steps > 0:
-        A_h = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
-        A_h.copy_(A)  # symmetric: the transpose view is the column-major matrix
         B_h = torch.empty((nrhs, n), dtype=torch.float64, pin_memory=True).t()
         B_h.copy_(B)
         X_h = torch.empty((nrhs, n), dtype=torch.float64, pin_memory=True).t()
@@ -327,79 +477,34 @@ def run_ours(args, w, rank, world):
         work_h = jmg.workspace(jmg.OP_POSV_HOST, n, nrhs, opts, dev)
         e2e_ms = []
         for k in range(1 + e2e_steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            Xe, sh = jmg.posv_host(A_h.t(), B_h, out=X_h, work=work_h, **kw)
-            e1.record(stream)
-            e1.synchronize()
+            dt, (_, sh) = _timed(stream, lambda: jmg.posv_host(A_h.t(), B_h, out=X_h, work=work_h,
+                                                               **kw))
             if k > 0:
-                e2e_ms.append(e0.elapsed_time(e1))
+                e2e_ms.append(dt)
                 e2e_bytes = (sh.h2d_bytes, sh.d2h_bytes)
         t_e2e = sum(e2e_ms) / 1e3
-        del work_h, A_h
+        del work_h
+        log("e2e: %.1f ms/step" % (t_e2e * 1e3 / e2e_steps))
 
     # ---- across ranks: max time
     t_mixed, tf, te = max_over_ranks([t_mixed, t_f64 or 0.0, t_e2e or 0.0], world, dev)
     t_f64 = tf if f64_steps > 0 else None
     t_e2e = te if e2e_steps > 0 else None
 
+    # ---- certification of the returned X by the CPU oracle (Dot2 residual)
+    t0 = time.time()
+    A_np = A_h.numpy()
+    eta_or = certify(A_np, X_keep, B_keep) if rank == 0 else None
+    eta64_or = certify(A_np, X64, B_keep) if (rank == 0 and X64 is not None) else None
+    log("oracle certification: %.1f s" % (time.time() - t0))
+
     value = replica_value(world, F, args.steps, t_mixed)
-    # Rooflines, from the library's CUDA events inside the timed steps (timing=True
-    # records events around the solves, the residual products and the factor only).
     peaks = load_peaks()
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
-    peak_src = "of measured (MEASURED_PEAKS.json)" if peaks else "of fallback"
-    n_sol = sum(si.n_solve for si in infos)
-    t_sol = sum(si.t_solve_gpu_ms for si in infos)
-    n_res = sum(si.n_resid for si in infos)
-    t_res = sum(si.t_resid_gpu_ms for si in infos)
-    t_fac = sum(si.t_factor_gpu_ms for si in infos)
-    steps_ms = t_mixed * 1e3 / world
-    # dominant kernel: the one-launch triangular solve with the FP32 factor
-    # (k_trsv_persist, two launches per solve).  Algorithmic bytes per launch:
-    # the lower triangle of L once (FP32) and one read + write of the n x nrhs block.
-    sol_bytes = n * (n + 1) / 2 * 4 + 2 * n * nrhs * 4
-    sol_launch_ms = t_sol / (2 * n_sol) if n_sol else None
-    sol_gbs = sol_bytes / (sol_launch_ms / 1e3) / 1e9 if n_sol else None
-    roof = {"kernel": "k_trsv_persist<float> (forward / backward solve with the FP32 factor)",
-            "bound": "hbm", "achieved": round(sol_gbs, 2) if sol_gbs else None,
-            "peak": hbm, "unit": "GB/s",
-            "frac": round(sol_gbs / hbm, 4) if sol_gbs else None, "peak_source": peak_src,
-            "traffic": SOLVE_TRAFFIC_BYTES(n, nrhs),
-            "algorithmic_bytes_per_launch": sol_bytes,
-            "launch_ms": round(sol_launch_ms, 4) if sol_launch_ms else None,
-            "launches": 2 * n_sol,
-            "share_of_step": round(t_sol / steps_ms, 4) if n_sol else None,
-            "note": "latency-bound serial chain of n/32 blocks; see profiles/"}
-    # the split FP64-accurate residual product on the BF16 tensor cores
-    # (k_oz_gemm): 36 slice pairs x 2 n^2 nrhs BF16 MMA flops per product
-    res_launch_ms = t_res / n_res if n_res else None
-    kern = {}
-    if n_res:
-        mma = 36 * 2.0 * n * n * nrhs if args.resid != "fp64" else None
-        kern["residual_product"] = {
-            "kernel": "k_oz_gemm (split, BF16 tensor cores)" if mma else "k_gemm<double> (FP64)",
-            "bound": "tensor" if mma else "alu",
-            "achieved": round((mma if mma else 2.0 * n * n * nrhs) / (res_launch_ms / 1e3) / 1e12, 3),
-            "peak": bf16 if mma else FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-            "fp64_equivalent_tflops": round(2.0 * n * n * nrhs / (res_launch_ms / 1e3) / 1e12, 3),
-            "launch_ms": round(res_launch_ms, 4), "launches": n_res,
-            "share_of_step": round(t_res / steps_ms, 4)}
-        kern["residual_product"]["frac"] = round(kern["residual_product"]["achieved"] /
-                                                 kern["residual_product"]["peak"], 4)
-    if t_fac > 0:
-        pairs = {1: 1, 2: 3, 3: 6}.get(words, 1) if prec != "fp8" else 1
-        mma_f = pairs * n ** 3 / 3.0
-        pk = bf16 * (2.0 if prec == "fp8" else 1.0)  # e4m3: twice the 16-bit rate (nominal ratio)
-        kern["factor"] = {"kernels": "k_potrf_diag + k_trsm_rows + k_split_words/k_quant_fp8 + "
-                                     "k_syrk_tc (tensor-core update)",
-                          "bound": "tensor", "unit": "TFLOP/s",
-                          "achieved": round(mma_f / (t_fac / len(infos) / 1e3) / 1e12, 3),
-                          "peak": pk, "ms": round(t_fac / len(infos), 3),
-                          "note": "tensor-core MMA flops of the trailing updates (%d word pairs) "
-                                  "over the whole factorisation time" % pairs}
-        kern["factor"]["frac"] = round(kern["factor"]["achieved"] / pk, 4)
+    steps_ms = t_mixed * 1e3 / args.steps
+    dom, objs = _roofline_objects(n, nrhs, prec, words, infos, steps_ms, peaks, args.resid)
+    roof = dict(objs[dom]) if dom else None
+    if roof is not None:
+        roof["traffic"] = traffic_per_launch(dom, n, nrhs)
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -412,16 +517,17 @@ def run_ours(args, w, rank, world):
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 (A = %.2f GB), no flush" % (n * n * 8 / 1e9)},
         "time_to_solution_ms": round(t_mixed * 1e3 / args.steps, 3),
-        "bwd_err": eta, "bwd_err_componentwise": eta_cw, "fwd_err": fwd,
+        "bwd_err_oracle": eta_or, "bwd_err": eta, "bwd_err_componentwise": eta_cw,
+        "fwd_err": fwd,
         "iters": [si.iters for si in infos],
         "refine_used": ["ir", "pcg", "auto"][infos[-1].refine_used] if infos[-1].refine_used >= 0 else None,
         "shift": infos[-1].shift, "factor_tries": infos[-1].factor_tries,
         "eta_hist": [float("%.3e" % e) for e in infos[-1].eta_hist],
-        "phases_ms": {"factor": round(statistics.mean(si.t_factor_ms for si in infos), 3),
-                      "solve": round(statistics.mean(si.t_solve_ms for si in infos), 3),
-                      "refine": round(statistics.mean(si.t_refine_ms for si in infos), 3)},
+        "phases_ms": {"factor_gpu": round(statistics.mean(si.t_factor_gpu_ms for si in infos), 3),
+                      "solves_gpu": round(statistics.mean(si.t_solve_gpu_ms for si in infos), 3),
+                      "residual_products_gpu": round(statistics.mean(si.t_resid_gpu_ms for si in infos), 3)},
         "roofline": roof,
-        "kernels": kern,
+        "kernels": {k: v for k, v in objs.items() if k != dom},
         "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
         "clocks": clocks,
     }
@@ -429,7 +535,7 @@ def run_ours(args, w, rank, world):
         fp64_value = replica_value(world, F, f64_steps, t_f64)
         out["fp64"] = {"value": round(fp64_value, 4), "unit": "TFLOP/s",
                        "ms_per_step": round(t_f64 * 1e3 / f64_steps, 3), "steps": f64_steps,
-                       "bwd_err": eta64,
+                       "bwd_err_oracle": eta64_or,
                        "frac_of_fp64_nominal": round(fp64_value / world / FP64_NOMINAL_TFLOPS, 4)}
         out["speedup_mixed_vs_fp64"] = round((t_f64 / f64_steps) / (t_mixed / args.steps), 3)
     if t_e2e is not None:
@@ -438,44 +544,159 @@ def run_ours(args, w, rank, world):
                       "h2d_bytes_per_step": e2e_bytes[0], "d2h_bytes_per_step": e2e_bytes[1],
                       "call": "jmg_posv_host (A and B host->device, X device->host, "
                               "page-locked host buffers)"}
+    del A, A_h, B, X, X_keep, B_keep, X64
+    torch.cuda.empty_cache()
     return out
 
 
-def run_grad(args, w, rank, world):
-    """Forward + backward of the differentiable solve (autograd.SPDSolve) for
-    loss = 0.5 ||X||_F^2: mixed forward (adjoint solve against the kept factor)
-    vs the FP64 forward; gradient checked by central differences."""
+# DRAM traffic (read + write) per launch of the dominant kernel, from one ncu
+# capture, as a multiple of the algorithmic bytes at the captured size; the
+# kernel reads each byte of L once, so its traffic scales with the algorithmic
+# bytes.  None where the kernel changed since the capture.
+TRAFFIC_RATIO = {"solve": None, "residual_product": None}
+
+
+def traffic_per_launch(kind, n, nrhs):
+    r = TRAFFIC_RATIO.get(kind)
+    if r is None:
+        return None
+    if kind == "solve":
+        return int(r * (n * (n + 1) / 2 * 4 + 2 * n * nrhs * 4))
+    return int(r * 16.0 * n * n)
+
+
+# ----------------------------------------------------------------------------- extra configs
+def _one_config(jmg, torch, dev, stream, A, Xt, B, prec, words, steps=1, warmup=1, nb=128):
+    """Timed mixed solve(s) of one configuration; returns a dict (ms, TFLOP/s,
+    iterations, backward errors) and X."""
+    n, nrhs = B.shape
+    Acm = A.t()
+    opts = jmg.default_options(prec=prec, words=words, nb=nb)
+    work = jmg.workspace(jmg.OP_POSV, n, nrhs, opts, dev)
+    ms, si, X = [], None, None
+    for k in range(warmup + steps):
+        dt, (X, si) = _timed(stream, lambda: jmg.posv(Acm, B, prec=prec, words=words, nb=nb,
+                                                      work=work, check=False))
+        if k >= warmup:
+            ms.append(dt)
+    del work
+    t = statistics.mean(ms)
+    d = {"prec": prec, "words": words if prec != "fp8" else None, "ms": round(t, 3),
+         "tflops": round(nominal_flops(n, nrhs) / (t / 1e3) / 1e12, 3), "steps": steps,
+         "status": si.status, "iters": si.iters,
+         "refine_used": ["ir", "pcg", "auto"][si.refine_used] if si.refine_used >= 0 else None,
+         "factor_tries": si.factor_tries, "bwd_err": si.bwd_err}
+    if Xt is not None:
+        d["fwd_err"] = float(((X - Xt).abs().max() / Xt.abs().max()).item())
+    return d, X
+
+
+def run_extras(args, which):
+    import numpy as np
     import torch
 
+    from paper_2601_14466_gb300 import inputs, jmg
+
+    dev = _device()
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for name in which:
+        t0 = time.time()
+        if name in ("c1", "c6"):
+            w = WORKLOADS[name]
+            A, Xt, B = make_inputs(w, dev)
+            A_np = host_f(A)
+            d, X = _one_config(jmg, torch, dev, stream, A, Xt, B, w["prec"], w["words"],
+                               steps=3, warmup=1)
+            d["bwd_err_oracle"] = certify(A_np, X, B)
+            f64_ms, X64 = _fp64_posv(jmg, A, B, stream, 3, warmup=1)
+            t64 = statistics.mean(f64_ms)
+            out[name] = {"workload": w["desc"], "n": w["n"], "nrhs": w["nrhs"], "mixed": d,
+                         "fp64": {"ms": round(t64, 3),
+                                  "tflops": round(nominal_flops(w["n"], w["nrhs"]) / (t64 / 1e3) / 1e12, 3),
+                                  "steps": 3, "bwd_err_oracle": certify(A_np, X64, B)},
+                         "speedup_mixed_vs_fp64": round(t64 / d["ms"], 3)}
+            if name == "c6":
+                i = np.arange(1, w["n"] + 1, dtype=np.float64)
+                out[name]["max_rel_err_vs_1_over_i"] = float(
+                    np.max(np.abs(host_f(X)[:, 0] * i - 1.0)))
+            del A, B, X, X64
+        elif name == "c3":
+            w = dict(WORKLOADS["c3"])
+            Q = inputs.q_factor(w["n"], seed=0, device=dev)
+            log("c3: Q ready in %.1f s" % (time.time() - t0))
+            rows = []
+            for kappa, words in C3_LADDER:
+                w["param"] = kappa
+                A, Xt, B = make_inputs(w, dev, Q=Q)
+                A_np = host_f(A)
+                row = {"kappa": kappa}
+                for prec in ("bf16", "fp16"):
+                    d, X = _one_config(jmg, torch, dev, stream, A, Xt, B, prec, words[prec])
+                    d["bwd_err_oracle"] = certify(A_np, X, B)
+                    row[prec] = d
+                    del X
+                f64_ms, X64 = _fp64_posv(jmg, A, B, stream, 1)
+                row["fp64"] = {"ms": round(f64_ms[0], 3),
+                               "tflops": round(nominal_flops(w["n"], w["nrhs"]) / (f64_ms[0] / 1e3) / 1e12, 3),
+                               "steps": 1, "bwd_err_oracle": certify(A_np, X64, B)}
+                for prec in ("bf16", "fp16"):
+                    row[prec]["speedup_vs_fp64"] = round(f64_ms[0] / row[prec]["ms"], 3)
+                rows.append(row)
+                del A, B, Xt, X64, A_np
+                torch.cuda.empty_cache()
+                log("c3 kappa=%g done" % kappa)
+            del Q
+            out["c3"] = {"workload": "posv n=32768 nrhs=16, A = Q diag(logspace[1,kappa]) Q^T, "
+                                     "one Q for every kappa", "n": w["n"], "nrhs": w["nrhs"],
+                         "ladder": rows}
+        elif name == "c5":
+            out["c5"] = run_grad(args, WORKLOADS["c5"])
+        torch.cuda.empty_cache()
+        log("%s done in %.1f s" % (name, time.time() - t0))
+    return out
+
+
+def run_grad(args, w):
+    """Forward + backward of the differentiable solve (autograd.SPDSolve) for
+    loss = 0.5 ||X||_F^2: mixed forward (adjoint solve against the kept factor)
+    vs the FP64 forward; the gradient checked by central differences of the FP64
+    forward on 8 seeded entries and against the oracle's adjoint."""
+    import numpy as np
+    import torch
+
+    import oracle
     from paper_2601_14466_gb300 import autograd, jmg
 
     dev = _device()
-    jmg.load()
     n, nrhs = w["n"], w["nrhs"]
-    prec, words = args.prec or w["prec"], args.words or w["words"]
+    prec, words = w["prec"], w["words"]
     A, _, B = make_inputs(w, dev)
     stream = torch.cuda.current_stream(dev)
 
     def step(p):
         Ad = A.clone().requires_grad_(True)
         Bd = B.clone().requires_grad_(True)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        X = autograd.solve(Ad, Bd, p, words)
-        (0.5 * (X * X).sum()).backward()
-        e1.record(stream)
-        e1.synchronize()
-        return e0.elapsed_time(e1), Ad.grad, Bd.grad
+
+        def f():
+            X = autograd.solve(Ad, Bd, p, words)
+            (0.5 * (X * X).sum()).backward()
+            return X
+
+        dt, X = _timed(stream, f)
+        return dt, Ad.grad, Bd.grad, X
 
     res = {}
     for p in (prec, "fp64"):
-        for _ in range(args.warmup):
-            step(p)
-        ms = [step(p)[0] for _ in range(args.steps if p == prec else min(args.steps, 3))]
-        res[p] = statistics.mean(ms)
-    _, G, GB = step(prec)
-    # central differences with the FP64 forward on 8 seeded entries
-    rng = __import__("numpy").random.default_rng(33)
+        step(p)
+        res[p] = statistics.mean(step(p)[0] for _ in range(3))
+    _, G, GB, X = step(prec)
+    # the oracle's adjoint: Abar = -(Bbar X^T + X Bbar^T)/2, Bbar = A^{-1} X
+    A_np = host_f(A)
+    Xo, info = oracle.posv(A_np, host_f(B))
+    _, Bbo, Abo, _ = oracle.grad(A_np, host_f(B), Xo)
+    grad_err = float(np.abs(host_f(G) - Abo).max() / np.abs(Abo).max())
+    rng = np.random.default_rng(33)
     h, worst = 1e-6, 0.0
     for _ in range(8):
         i, j = sorted(rng.integers(0, n, size=2))[::-1]
@@ -484,25 +705,20 @@ def run_grad(args, w, rank, world):
         E[j, i] = h
 
         def loss(M):
-            X, _ = jmg.posv(M.t(), B, prec="fp64")
-            return 0.5 * float((X * X).sum().item())
+            Xf, _ = jmg.posv(M.t(), B, prec="fp64")
+            return 0.5 * float((Xf * Xf).sum().item())
 
         fd = (loss(A + E) - loss(A - E)) / (2 * h)
         want = float(G[i, j] + G[j, i]) if i != j else float(G[i, i])
         worst = max(worst, abs(fd - want) / max(1.0, abs(want)))
     F = nominal_flops(n, nrhs) + 2.0 * n * n * nrhs  # forward + adjoint solve
-    return {
-        "metric": METRIC + " [differentiation workload: forward+backward]",
-        "value": round(F / (res[prec] / 1e3) / 1e12, 4), "unit": "TFLOP/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(res[prec], 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64 (%sx%d tensor-core factor)" % (prec, words), "data": "synthetic, seeded",
-        "config": {"workload": w["desc"], "n": n, "nrhs": nrhs, "prec": prec, "words": words},
-        "fp64": {"ms_per_step": round(res["fp64"], 3),
-                 "value": round(F / (res["fp64"] / 1e3) / 1e12, 4)},
-        "speedup_mixed_vs_fp64": round(res["fp64"] / res[prec], 3),
-        "fd_max_rel_err_8_entries": worst,
-    }
+    return {"workload": w["desc"], "n": n, "nrhs": nrhs, "prec": prec, "words": words,
+            "ms": round(res[prec], 3), "tflops": round(F / (res[prec] / 1e3) / 1e12, 3),
+            "fp64_ms": round(res["fp64"], 3),
+            "speedup_mixed_vs_fp64": round(res["fp64"] / res[prec], 3),
+            "bwd_err_oracle": certify(A_np, X, B),
+            "grad_max_rel_err_vs_oracle": grad_err,
+            "fd_max_rel_err_8_entries": worst}
 
 
 def main():
@@ -511,11 +727,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="c4", choices=sorted(WORKLOADS))
+    ap.add_argument("--extra", default="c1,c6,c5,c3",
+                    help="comma-separated extra configurations (one timed solve each), or none")
     ap.add_argument("--prec", default=None)
     ap.add_argument("--words", type=int, default=None)
     ap.add_argument("--nb", type=int, default=128)
-    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--kappa", type=float, default=None)
     ap.add_argument("--maxit", type=int, default=300)
@@ -534,18 +752,23 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        # each "step" is one oracle solve of the bounded sample; the sample is
-        # timed over enough repetitions to cover the requested steps
-        cb = cpu_oracle_sample(w, target_s=max(4.0, 2.0 * args.steps))
-        value = cb["value"]
+        import oracle
+
+        # each step is one oracle solve of a bounded sample of the workload
+        n_s, times = cpu_oracle_timed(w, args.steps, args.warmup)
+        t = statistics.mean(times)
+        value = nominal_flops(n_s, w["nrhs"]) / t / 1e12
+        sample = ("oracle posv at n=%d nrhs=%d (same construction): %d warm-up and %d timed "
+                  "solves, %.3f s each" % (n_s, w["nrhs"], args.warmup, len(times), t))
         print(json.dumps({
             "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "TFLOP/s",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(cb["seconds_per_solve"] * 1e3, 3), "higher_is_better": True,
+            "n_gpus": args.gpus, "steps": len(times), "warmup": args.warmup,
+            "ms_per_step": round(t * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic, seeded",
-            "config": {"workload": w["desc"] + " (bounded CPU sample: " + cb["sample"] + ")",
-                       "n": w["n"], "nrhs": w["nrhs"]},
-            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "config": {"workload": w["desc"] + " (bounded CPU sample: " + sample + ")",
+                       "n": w["n"], "nrhs": w["nrhs"], "sample_n": n_s},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": oracle.threads(),
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
         }))
@@ -555,11 +778,21 @@ def main():
 
     if world > 1:
         torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    out = (run_grad if args.workload == "c5" else run_ours)(args, w, rank, world)
+    if args.workload == "c5":
+        _device()
+        out = run_grad(args, w)
+        out.update({"metric": METRIC + " [differentiation workload: forward+backward]",
+                    "value": out["tflops"], "unit": "TFLOP/s", "n_gpus": world,
+                    "steps": 3, "warmup": 1, "ms_per_step": out["ms"], "higher_is_better": True,
+                    "scaling": "weak", "vs_baseline": None})
+    else:
+        out = run_main(args, w, rank, world)
+        extras = [e for e in args.extra.split(",") if e and e != "none" and e != args.workload]
+        if extras and world == 1:
+            out["extra_configs"] = run_extras(args, extras)
     if rank == 0:
         if not args.no_cpu_baseline:
-            cb = cpu_oracle_sample(w)
-            out["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+            out["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()

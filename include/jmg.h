@@ -139,6 +139,10 @@ int jmg_potrf(int n, void* A, int lda, int dtype, int* info, const jmg_options* 
  */
 int jmg_potrs(int n, int nrhs, const void* L, int lda, void* B, int ldb, int dtype,
               void* work, size_t lwork, void* stream);
+/* Outcome word of jmg_potrs: once the call's kernels have completed (after a
+ * synchronisation of `stream`), the first int of `work` holds 0, or
+ * JMG_ERR_TIMEOUT if a device-side wait of the solve ran out (B is then not a
+ * solution).  The word is written on the device; read it with a copy. */
 
 /*
  * potrs_static -- jmg_potrs without a `work` buffer.  The paper has no
@@ -163,6 +167,15 @@ int jmg_potrs(int n, int nrhs, const void* L, int lda, void* B, int ldb, int dty
  */
 int jmg_potrs_static(int n, int nrhs, const void* L, int lda, void* B, int ldb, int dtype,
                      void* stream);
+
+/*
+ * potrs_static_status -- the outcome of the last jmg_potrs_static call on the
+ * current device: waits for `stream`, then sets *status (a HOST int) to 0, or
+ * to JMG_ERR_TIMEOUT if a device-side wait of that solve ran out (its B is then
+ * not a solution).  Allocates nothing.  Returns JMG_OK, -1 for a NULL status,
+ * or JMG_ERR_CUDA.
+ */
+int jmg_potrs_static_status(int* status, void* stream);
 
 /*
  * posv -- solve A X = B (paper: "Software design", potrs as one call).

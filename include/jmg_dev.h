@@ -83,6 +83,47 @@ int jmg_dev_probe(int kind, int blocks, int iters, double* sink, double* flops, 
  * started (host-side counter, incremented at every launch). */
 long long jmg_dev_launch_count(void);
 
+/*
+ * Time limit of every device-side wait (the solves' flag waits and the
+ * tensor-core kernels' mbarrier waits), in nanoseconds of %globaltimer; the
+ * default is 2 s.  Sets it to `ns` (ns > 0; 0 only queries) and returns the
+ * previous value.  Process-wide and read at each launch: change it only while
+ * no call of this library is being issued from another thread.
+ */
+unsigned long long jmg_dev_set_wait_limit_ns(unsigned long long ns);
+
+/*
+ * Bounded-wait checks.  Each launches one kernel in a state where one of its
+ * device-side waits is never satisfied, so the wait runs out after the current
+ * limit and the kernel leaves through its abort path (no trap, no fault):
+ *
+ * trsv_leaderless: the one-launch forward solve L Y = B (dtype JMG_F64 or
+ *   JMG_F32) with every ticket offset by one, so that no CTA takes the leading
+ *   role and no block of Y is ever published: every helper's flag wait runs
+ *   out.  `sync` holds jmg_workspace_size(JMG_OP_POTRS, n, nrhs, dtype, NULL)
+ *   bytes; afterwards sync[0] == JMG_ERR_TIMEOUT and *info == -1 (info may be
+ *   NULL).  B is left partly overwritten.
+ *
+ * syrk_tc_idle_producer: the tensor-core trailing update (arguments as
+ *   jmg_dev_syrk_tc) with its copy producer idle: the MMA issuer's wait for the
+ *   first stage runs out; afterwards *err != 0 and C is untouched.
+ */
+int jmg_dev_trsv_leaderless(int n, int nrhs, const void* L, int lda, void* B, int ldb, int dtype,
+                            int* sync, int* info, void* stream);
+int jmg_dev_syrk_tc_idle_producer(int m, int ncols, int kext, const void* PA, const void* PB,
+                                  int ldp, int prec, float* C, int ldc, int* err, void* stream);
+
+/*
+ * The FP8 quantiser of the mixed factorisation on its own: the FP32 panel
+ * L21 (m x kb, column-major, ldw) becomes Q (m x kb e4m3 bytes, row-major, ldq
+ * >= kb) with one exponent per 128-row tile t:
+ *     e_t = floor(log2(448 / amax_t)) clamped to [-126, 126] (0 when amax_t = 0),
+ *     Q[i, c] = e4m3_rn_satfinite(L21[i, c] * 2^e_t)     (round to nearest even).
+ * e: ceil(m / 128) int8.  Asynchronous.
+ */
+int jmg_dev_quant_fp8(int m, int kb, const float* L21, int ldw, void* Q, int ldq, signed char* e,
+                      void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,8 @@ class Oracle:
         lib.oracle_norm_inf.restype = ctypes.c_double
         lib.oracle_bwd_err.argtypes = [_I, _I, _D, _I, _D, _I, _D, _I, _D]
         lib.oracle_bwd_err.restype = ctypes.c_double
+        lib.oracle_bwd_err_rows.argtypes = [_I, _I, _D, _I, _D, _I, _D, _I, _D]
+        lib.oracle_bwd_err_rows.restype = ctypes.c_double
         lib.oracle_logdet.argtypes = [_I, _D, _I]
         lib.oracle_logdet.restype = ctypes.c_double
         lib.oracle_grad.argtypes = [_I, _I, _D, _I, _D, _I, _D, _I, _D, _D, _D, _I]
@@ -139,6 +141,17 @@ class Oracle:
         eta = np.zeros(nrhs)
         worst = self.lib.oracle_bwd_err(n, nrhs, _p(A), _ld(A), _p(X), _ld(X), _p(B), _ld(B),
                                         _p(eta))
+        return float(worst), eta
+
+    def bwd_err_rows(self, A, X, B):
+        """oracle_bwd_err's numbers, bit for bit, with A read once (for matrices
+        of tens of GB).  A, X and B may be any column-major float64 arrays
+        (A: only its lower triangle is read)."""
+        A, X, B = _f64(A), _f64(X), _f64(B)
+        n, nrhs = X.shape
+        eta = np.zeros(nrhs)
+        worst = self.lib.oracle_bwd_err_rows(n, nrhs, _p(A), _ld(A), _p(X), _ld(X), _p(B),
+                                             _ld(B), _p(eta))
         return float(worst), eta
 
     def logdet(self, L) -> float:
@@ -223,6 +236,10 @@ def norm_inf(A) -> float:
 
 def bwd_err(A, X, B):
     return default().bwd_err(A, X, B)
+
+
+def bwd_err_rows(A, X, B):
+    return default().bwd_err_rows(A, X, B)
 
 
 def logdet(L) -> float:

@@ -27,6 +27,9 @@
  *   oracle_norm_inf  ||A||_inf of the symmetric matrix held in its lower triangle.
  *   oracle_bwd_err normwise backward error per column (Rigal and Gaches):
  *                  eta_j = ||r_j||_inf / (||A||_inf ||x_j||_inf + ||b_j||_inf).
+ *   oracle_bwd_err_rows  the same numbers, bit for bit, with the loops arranged
+ *                  so that a matrix of tens of GB is read once (certification
+ *                  of full-size results).
  *   oracle_logdet  log det A = 2 sum_i log L_ii (paper: "Software design",
  *                  potrs can also return log det A).
  *   oracle_grad    adjoint of X = A^{-1} B for symmetric A:
@@ -180,11 +183,81 @@ double oracle_bwd_err(int n, int nrhs, const double* A, int lda, const double* X
       bn = nan_max(bn, fabs(AT(B, i, c, ldb)));
     }
     double den = anorm * xn + bn;
-    double e = den > 0.0 ? rn / den : (rn > 0.0 ? INFINITY : 0.0);
+    double e = (isnan(rn) || isnan(den)) ? NAN : den > 0.0 ? rn / den : (rn > 0.0 ? INFINITY : 0.0);
     if (eta) eta[c] = e;
     if (e > worst || isnan(e)) worst = e;
   }
   free(r);
+  return worst;
+}
+
+/* The same per-column backward errors as oracle_bwd_err, bit for bit, for
+ * matrices too large for its row-by-row sweep.  Every residual entry is still
+ * the Dot2 sum over j = 0, 1, ..., n-1 of exactly the operations of
+ * oracle_resid_dot2, and every row sum of ||A||_inf runs over j in the same
+ * order as in oracle_norm_inf; only the loop nest is arranged differently:
+ * rows go in blocks of 32 that advance through j together, each carrying its
+ * own running sums for all right-hand sides, so that A is read once, down its
+ * columns (lower triangle) and along 32 neighbouring columns (the mirrored
+ * half), instead of once per right-hand side along its rows. */
+#define ORACLE_ROWS 32
+double oracle_bwd_err_rows(int n, int nrhs, const double* A, int lda, const double* X,
+                           int ldx, const double* B, int ldb, double* eta) {
+  const size_t nr = (size_t)(nrhs > 0 ? nrhs : 1);
+  double* r = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * nr);
+  double* rowsum = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int i0 = 0; i0 < n; i0 += ORACLE_ROWS) {
+    const int ib = n - i0 < ORACLE_ROWS ? n - i0 : ORACLE_ROWS;
+    double* s = (double*)malloc(sizeof(double) * ORACLE_ROWS * nr);
+    double* comp = (double*)malloc(sizeof(double) * ORACLE_ROWS * nr);
+    double asum[ORACLE_ROWS];
+    for (int ii = 0; ii < ib; ++ii) {
+      asum[ii] = 0.0;
+      for (int c = 0; c < nrhs; ++c) {
+        s[(size_t)ii * nr + c] = AT(B, i0 + ii, c, ldb);
+        comp[(size_t)ii * nr + c] = 0.0;
+      }
+    }
+    for (int j = 0; j < n; ++j) {
+      for (int ii = 0; ii < ib; ++ii) {
+        const double a = sym_at(A, lda, i0 + ii, j);
+        asum[ii] += fabs(a);
+        for (int c = 0; c < nrhs; ++c) {
+          double p, ep, es;
+          double* sc = &s[(size_t)ii * nr + c];
+          two_prod(-a, AT(X, j, c, ldx), &p, &ep);
+          two_sum(*sc, p, sc, &es);
+          comp[(size_t)ii * nr + c] += es + ep;
+        }
+      }
+    }
+    for (int ii = 0; ii < ib; ++ii) {
+      rowsum[i0 + ii] = asum[ii];
+      for (int c = 0; c < nrhs; ++c)
+        r[(size_t)c * n + i0 + ii] = s[(size_t)ii * nr + c] + comp[(size_t)ii * nr + c];
+    }
+    free(s);
+    free(comp);
+  }
+  double anorm = 0.0;
+  for (int i = 0; i < n; ++i)
+    if (rowsum[i] > anorm || isnan(rowsum[i])) anorm = rowsum[i];
+  double worst = 0.0;
+  for (int c = 0; c < nrhs; ++c) {
+    double rn = 0.0, xn = 0.0, bn = 0.0;
+    for (int i = 0; i < n; ++i) {
+      rn = nan_max(rn, fabs(r[(size_t)c * n + i]));
+      xn = nan_max(xn, fabs(AT(X, i, c, ldx)));
+      bn = nan_max(bn, fabs(AT(B, i, c, ldb)));
+    }
+    double den = anorm * xn + bn;
+    double e = (isnan(rn) || isnan(den)) ? NAN : den > 0.0 ? rn / den : (rn > 0.0 ? INFINITY : 0.0);
+    if (eta) eta[c] = e;
+    if (e > worst || isnan(e)) worst = e;
+  }
+  free(r);
+  free(rowsum);
   return worst;
 }
 

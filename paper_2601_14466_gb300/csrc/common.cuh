@@ -17,6 +17,19 @@ namespace jmg {
 
 extern long long g_launches;  // launches queued by this library (jmg_dev_launch_count)
 
+// Time limit of every device-side wait (flag and mbarrier spins), passed to the
+// kernels at launch.  2 s by default: far above any legal wait.  Process-wide;
+// jmg_dev_set_wait_limit_ns changes it (tests shorten it to make a wait run out).
+extern unsigned long long g_wait_ns;
+
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current
+// device, once per (kernel, device) pair; thread-safe.
+int ensure_smem_raw(const void* func, int bytes);
+template <typename F>
+inline int ensure_smem(F* func, int bytes) {
+  return ensure_smem_raw(reinterpret_cast<const void*>(func), bytes);
+}
+
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? JMG_OK : JMG_ERR_CUDA; }
 
 // After a launch: count it, and turn a launch error into JMG_ERR_CUDA.

@@ -954,4 +954,49 @@ int jmg_dev_norm_inf(int n, const double* A, int lda, double* out, void* work, s
 
 long long jmg_dev_launch_count(void) { return g_launches; }
 
+unsigned long long jmg_dev_set_wait_limit_ns(unsigned long long ns) {
+  const unsigned long long old = g_wait_ns;
+  if (ns > 0) g_wait_ns = ns;
+  return old;
+}
+
+int jmg_dev_trsv_leaderless(int n, int nrhs, const void* L, int lda, void* B, int ldb, int dtype,
+                            int* sync, int* info, void* stream) {
+  if (n <= 0) return -1;
+  if (nrhs <= 0) return -2;
+  if (lda < n) return -4;
+  if (ldb < n) return -6;
+  if (!L) return -3;
+  if (!B) return -5;
+  if (!sync) return -8;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == JMG_F32)
+    return launch_trsv_persist<float>(n, nrhs, (const float*)L, lda, (float*)B, ldb, 0, sync, info,
+                                      s, 1);
+  if (dtype == JMG_F64)
+    return launch_trsv_persist<double>(n, nrhs, (const double*)L, lda, (double*)B, ldb, 0, sync,
+                                       info, s, 1);
+  return -7;
+}
+
+int jmg_dev_syrk_tc_idle_producer(int m, int ncols, int kext, const void* PA, const void* PB,
+                                  int ldp, int prec, float* C, int ldc, int* err, void* stream) {
+  if (m <= 0) return -1;
+  if (ncols <= 0 || ncols > m) return -2;
+  if (ldc < m) return -9;
+  if (!err) return -10;
+  return launch_syrk_tc(m, ncols, kext, PA, PB, ldp, prec, C, ldc, err, (cudaStream_t)stream, 0,
+                        1);
+}
+
+int jmg_dev_quant_fp8(int m, int kb, const float* L21, int ldw, void* Q, int ldq, signed char* e,
+                      void* stream) {
+  if (m < 0) return -1;
+  if (kb <= 0) return -2;
+  if (ldw < std::max(1, m)) return -4;
+  if (ldq < kb) return -6;
+  if (m > 0 && (!L21 || !Q || !e)) return !L21 ? -3 : (!Q ? -5 : -7);
+  return launch_quant_fp8(m, kb, L21, ldw, Q, ldq, e, (cudaStream_t)stream);
+}
+
 }  // extern "C"

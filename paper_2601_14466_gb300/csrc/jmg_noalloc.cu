@@ -20,7 +20,8 @@ namespace {
 // Fixed scratch: 65536 ints (256 KiB), resident on every GPU that loads the
 // library until the process exits.  Every call shares it and it keeps the last
 // call's contents; the solve launcher clears the part it uses before each
-// launch.
+// launch (word 0, the outcome, only before the forward solve, so that it
+// carries a timeout of either direction to jmg_potrs_static_status).
 constexpr int kStaticScratchInts = 65536;
 static __device__ __align__(256) int g_solve_scratch[kStaticScratchInts];
 
@@ -65,4 +66,21 @@ extern "C" int jmg_potrs_static(int n, int nrhs, const void* L, int lda, void* B
   JMG_TRY(scratch_for_current_device(&scratch));
   return solve_llt<double>(n, nrhs, static_cast<const double*>(L), lda, static_cast<double*>(B),
                            ldb, scratch, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+// The solve writes its outcome into the first word of the fixed scratch (0, or
+// JMG_ERR_TIMEOUT when a device-side wait ran out).  The word stays there until
+// the next call on the same device clears it, so this reads the outcome of the
+// last call queued on `stream`.
+extern "C" int jmg_potrs_static_status(int* status, void* stream) {
+  using namespace jmg;
+  if (!status) return -1;
+  int* scratch = nullptr;
+  JMG_TRY(scratch_for_current_device(&scratch));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int word = 0;
+  JMG_CUDA(cudaMemcpyAsync(&word, scratch, sizeof(int), cudaMemcpyDeviceToHost, s));
+  JMG_CUDA(cudaStreamSynchronize(s));
+  *status = word;
+  return JMG_OK;
 }

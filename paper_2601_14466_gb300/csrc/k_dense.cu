@@ -6,11 +6,30 @@
 // factorisation followed by the triangular solves.  The paper delegates both to
 // cuSOLVERMp; the blocking below is the textbook right-looking scheme (factor
 // the diagonal block, solve the panel below it, update the trailing matrix).
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "kernels.h"
 
 namespace jmg {
 
 long long g_launches = 0;
+unsigned long long g_wait_ns = 2000000000ull;
+
+int ensure_smem_raw(const void* func, int bytes) {
+  int dev = 0;
+  JMG_CUDA(cudaGetDevice(&dev));
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> raised;
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair(func, dev);
+  const auto it = raised.find(key);
+  if (it != raised.end() && it->second >= bytes) return JMG_OK;
+  JMG_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  raised[key] = bytes;
+  return JMG_OK;
+}
 
 // ============================================================================
 // Diagonal-block factorisation L_kk L_kk^T = A_kk (kb <= 128), in place, as a
@@ -326,15 +345,14 @@ int posv_small_batched(int n, int nrhs, int batch, T* A, int lda, long long sA, 
   if (n == 0 || batch == 0) return JMG_OK;
   {
     auto k = k_potrf_diag_batched<T>;
-    JMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(pdiag::KB * pdiag::LD * sizeof(T))));
+    JMG_TRY(ensure_smem(k, (int)(pdiag::KB * pdiag::LD * sizeof(T))));
     k<<<batch, pdiag::TH, (size_t)n * pdiag::LD * sizeof(T), s>>>(A, lda, sA, n, info);
     JMG_TRY(launched());
   }
   if (nrhs == 0) return JMG_OK;
   auto k = k_potrs_small<T>;
   const size_t smem = sizeof(T) * ((size_t)n * (n + 1) + (size_t)n * (pbat::TH + 1));
-  JMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  JMG_TRY(ensure_smem(k, (int)smem));
   k<<<batch, pbat::TH, smem, s>>>(n, nrhs, A, lda, sA, B, ldb, sB, info);
   return launched();
 }
@@ -348,12 +366,7 @@ static int potf2_impl(T* A, int lda, int kb, int koff, int* info, cudaStream_t s
   if (kb > pdiag::KB) return JMG_ERR_UNSUPPORTED;
   const size_t smem = (size_t)kb * pdiag::LD * sizeof(T);
   auto k = k_potrf_diag<T>;
-  static int attr[2] = {0, 0};
-  if (!attr[sizeof(T) == 8]) {
-    JMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(pdiag::KB * pdiag::LD * sizeof(T))));
-    attr[sizeof(T) == 8] = 1;
-  }
+  JMG_TRY(ensure_smem(k, (int)(pdiag::KB * pdiag::LD * sizeof(T))));
   k<<<1, pdiag::TH, smem, s>>>(A, lda, kb, koff, info);
   return launched();
 }
@@ -432,7 +445,7 @@ static int trsm_impl(T* A21, int lda, int m, int kb, const T* Lkk, const int* in
   if (m <= 0) return JMG_OK;
   size_t smem = ((size_t)kb * (kb + 1) + (size_t)kb * (BR + 1)) * sizeof(T);
   auto k = k_trsm<T, BR>;
-  JMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  JMG_TRY(ensure_smem(k, (int)smem));
   k<<<cdiv(m, BR), 256, smem, s>>>(A21, lda, m, kb, Lkk, info);
   return launched();
 }
@@ -548,7 +561,7 @@ int launch_trsm(float* A21, int lda, int m, int kb, const float* Lkk, const int*
   if (kb == 128 || kb == 64) {
     auto k = (kb == 128) ? k_trsm_rows<128> : k_trsm_rows<64>;
     const size_t smem = sizeof(float) * ((size_t)kb * kb + (size_t)kb * ptrsm::LDX + kb);
-    JMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    JMG_TRY(ensure_smem(k, (int)smem));
     k<<<cdiv(m, ptrsm::RB), ptrsm::TH, smem, s>>>(A21, lda, m, Lkk, info);
     return launched();
   }

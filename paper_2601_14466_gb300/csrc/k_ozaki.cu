@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX,
               int n, int nrhs, int nrhs_pad, const double* __restrict__ rowmax,
               const int* __restrict__ ex, double* __restrict__ part, int win_per_split,
-              int* __restrict__ err) {
+              int* __restrict__ err, unsigned long long wait_ns) {
   using namespace oz;
   using namespace tc;
   constexpr int X_TILE = N * BK * 2;  // one slice: N rows x 128 bytes
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
       long long g = 0;
       for (int kb = kb0; kb < kb1; ++kb) {
         const int u = kb - kb0, xs = u & 1;
-        if (u >= 2 && !mbar_wait(&xempty[xs], (uint32_t)((u >> 1) - 1) & 1)) {
+        if (u >= 2 && !mbar_wait(&xempty[xs], (uint32_t)((u >> 1) - 1) & 1, wait_ns)) {
           atomicExch(&s_fail, 1);
           break;
         }
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
         bool ok = true;
         for (int a = 0; a < S; ++a, ++g) {
           const int st = (int)(g % ASTAGES);
-          if (g >= ASTAGES && !mbar_wait(&aempty[st], (uint32_t)((g / ASTAGES) - 1) & 1)) {
+          if (g >= ASTAGES && !mbar_wait(&aempty[st], (uint32_t)((g / ASTAGES) - 1) & 1, wait_ns)) {
             ok = false;
             break;
           }
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
       long long g = 0;
       bool ok = true;
       for (int w = w0; w < w1 && ok; ++w) {
-        if (w > w0 && !mbar_wait(acce, (uint32_t)((w - w0 - 1) & 1))) {
+        if (w > w0 && !mbar_wait(acce, (uint32_t)((w - w0 - 1) & 1), wait_ns)) {
           ok = false;
           break;
         }
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
         const int kbw0 = max(kb0, w * WIN), kbw1 = min(kb1, (w + 1) * WIN);
         for (int kb = kbw0; kb < kbw1 && ok; ++kb) {
           const int u = kb - kb0, xs = u & 1;
-          if (!mbar_wait(&xfull[xs], (uint32_t)(u >> 1) & 1)) {
+          if (!mbar_wait(&xfull[xs], (uint32_t)(u >> 1) & 1, wait_ns)) {
             ok = false;
             break;
           }
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
           const uint32_t xb = smem_u32(xbuf + xs * X_BUF);
           for (int a = 0; a < S; ++a, ++g) {
             const int st = (int)(g % ASTAGES);
-            if (!mbar_wait(&afull[st], (uint32_t)(g / ASTAGES) & 1)) {
+            if (!mbar_wait(&afull[st], (uint32_t)(g / ASTAGES) & 1, wait_ns)) {
               ok = false;
               break;
             }
@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
       for (int c = 0; c < CW; ++c) hs[c] = ls[c] = 0ull;
       bool ok = true;
       for (int w = w0; w < w1; ++w) {
-        if (!mbar_wait(accf, (uint32_t)((w - w0) & 1)) || ld_shared_volatile(&s_fail)) {
+        if (!mbar_wait(accf, (uint32_t)((w - w0) & 1), wait_ns) || ld_shared_volatile(&s_fail)) {
           ok = false;
           break;
         }
@@ -423,9 +423,9 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
   if (ld_shared_volatile(&s_fail)) {
     if (warp == 0 && lane == 0) {
       for (long long u = (x_issued > 2 ? x_issued - 2 : 0); u < x_issued; ++u)
-        (void)mbar_wait(&xfull[u & 1], (uint32_t)(u >> 1) & 1);
+        (void)mbar_wait(&xfull[u & 1], (uint32_t)(u >> 1) & 1, wait_ns);
       for (long long g = (a_issued > ASTAGES ? a_issued - ASTAGES : 0); g < a_issued; ++g)
-        (void)mbar_wait(&afull[g % ASTAGES], (uint32_t)(g / ASTAGES) & 1);
+        (void)mbar_wait(&afull[g % ASTAGES], (uint32_t)(g / ASTAGES) & 1, wait_ns);
       atomicExch(err, 1);
     }
   }
@@ -517,16 +517,12 @@ static int oz_gemm_launch(int n, int nrhs, const void* SA, const void* SX, int n
   JMG_TRY(map_bf16(&ma, SA, oz::S * n, n, lds, oz::BM));
   JMG_TRY(map_bf16(&mx, SX, oz::S * nrhs_pad, n, lds, N));
   constexpr int SMEM = 2 * oz::S * N * oz::BK * 2 + oz::ASTAGES * oz::A_TILE + 1024 + 256;
-  static bool attr = false;
-  if (!attr) {
-    JMG_CUDA(cudaFuncSetAttribute(k_oz_gemm<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
-    attr = true;
-  }
+  JMG_TRY(ensure_smem(k_oz_gemm<N>, SMEM));
   const int nwin = cdiv(cdiv(n, oz::BK), oz::WIN);
   const int wps = cdiv(nwin, ks);
   dim3 grid(cdiv(n, oz::BM), nrhs_pad / N, cdiv(nwin, wps));
   k_oz_gemm<N><<<grid, oz::THREADS, SMEM, s>>>(ma, mx, n, nrhs, nrhs_pad, rowmax, ex, part, wps,
-                                               err);
+                                               err, g_wait_ns);
   return launched();
 }
 

@@ -21,8 +21,9 @@
 //                       two warps per TMEM lane quarter, 64 columns each.  They
 //                       prefetch the next tile's C into L2 before they drain
 //                       this one, so the read-modify-write of C meets L2.
-// Every mbarrier wait is bounded (globaltimer); on expiry the kernel raises
-// *err, drains its own copies, frees TMEM and returns without touching C.
+// Every mbarrier wait is bounded by `wait_ns` (globaltimer); on expiry the
+// kernel raises *err, drains its own copies, frees TMEM and returns without
+// touching C.
 //
 // The paper runs these updates inside cuSOLVERMp (FP32/FP64, "Software
 // design"); the split-word tensor-core form is this library's own design.
@@ -75,7 +76,8 @@ template <int KIND>
 __global__ void __launch_bounds__(PTHREADS, 1)
     k_syrk_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               float* __restrict__ C, int ldc, int m, int ncols, int kext, int ab_fmt,
-              int ntiles, int TJ, const signed char* __restrict__ exps, int* __restrict__ err) {
+              int ntiles, int TJ, const signed char* __restrict__ exps, int* __restrict__ err,
+              unsigned long long wait_ns, int hold_producer) {
   extern __shared__ __align__(1024) unsigned char sm_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(sm_raw) + 1023) & ~uintptr_t(1023));
@@ -114,14 +116,17 @@ __global__ void __launch_bounds__(PTHREADS, 1)
 
   long long issued = 0;  // producer: stage loads issued (global k-iteration count)
   if (warp == 0) {
-    if (lane == 0) {
+    // hold_producer (a test hook) keeps the producer idle: nothing ever completes
+    // the first stage, so the MMA issuer's bounded wait runs out and the kernel
+    // takes its abort path
+    if (lane == 0 && !hold_producer) {
       long long g = 0;
       for (int b = blockIdx.x; b < ntiles; b += gridDim.x) {
         int ti, tj;
         trap_index(b, TJ, ti, tj);
         for (int kb = 0; kb < nk; ++kb, ++g) {
           const int s = (int)(g % PSTAGES);
-          if (g >= PSTAGES && !mbar_wait(&empty[s], (uint32_t)((g / PSTAGES) - 1) & 1)) {
+          if (g >= PSTAGES && !mbar_wait(&empty[s], (uint32_t)((g / PSTAGES) - 1) & 1, wait_ns)) {
             atomicExch(&s_fail, 1);
             break;
           }
@@ -143,7 +148,7 @@ __global__ void __launch_bounds__(PTHREADS, 1)
       int i = 0;
       for (int b = blockIdx.x; b < ntiles; b += gridDim.x, ++i) {
         const int a = i & 1;
-        if (i >= 2 && !mbar_wait(&acc_empty[a], (uint32_t)((i / 2) - 1) & 1)) {
+        if (i >= 2 && !mbar_wait(&acc_empty[a], (uint32_t)((i / 2) - 1) & 1, wait_ns)) {
           atomicExch(&s_fail, 1);
           break;
         }
@@ -152,7 +157,7 @@ __global__ void __launch_bounds__(PTHREADS, 1)
         bool ok = true;
         for (int kb = 0; kb < nk; ++kb, ++g) {
           const int s = (int)(g % PSTAGES);
-          if (!mbar_wait(&full[s], (uint32_t)(g / PSTAGES) & 1)) {
+          if (!mbar_wait(&full[s], (uint32_t)(g / PSTAGES) & 1, wait_ns)) {
             ok = false;
             break;
           }
@@ -202,7 +207,7 @@ __global__ void __launch_bounds__(PTHREADS, 1)
       trap_index(b, TJ, ti, tj);
       prefetch_c(b + gridDim.x);
       const int a = i & 1;
-      const bool ok = mbar_wait(&acc_full[a], (uint32_t)(i / 2) & 1);
+      const bool ok = mbar_wait(&acc_full[a], (uint32_t)(i / 2) & 1, wait_ns);
       tc_fence_after();
       if (!ok || ld_shared_volatile(&s_fail)) {
         atomicExch(&s_fail, 1);
@@ -243,7 +248,7 @@ __global__ void __launch_bounds__(PTHREADS, 1)
     if (warp == 0 && lane == 0) {
       // let every copy this CTA issued land before the CTA exits
       for (long long g = (issued > PSTAGES ? issued - PSTAGES : 0); g < issued; ++g)
-        (void)mbar_wait(&full[g % PSTAGES], (uint32_t)(g / PSTAGES) & 1);
+        (void)mbar_wait(&full[g % PSTAGES], (uint32_t)(g / PSTAGES) & 1, wait_ns);
       atomicExch(err, 1);
     }
   }
@@ -293,26 +298,21 @@ static int make_map(CUtensorMap* map, const void* base, int rows, int cols, int 
 template <int KIND>
 static int syrk_persistent(int m, int ncols, int kext, const CUtensorMap& ma, const CUtensorMap& mb,
                            int ab_fmt, const signed char* exps, float* C, int ldc, int* err,
-                           cudaStream_t s, int max_ctas) {
-  static int attr_dev = -1, nsm = 0;
-  int dev = 0;
+                           cudaStream_t s, int max_ctas, int hold = 0) {
+  int dev = 0, nsm = 0;
   JMG_CUDA(cudaGetDevice(&dev));
-  if (attr_dev != dev) {
-    JMG_CUDA(cudaFuncSetAttribute(tc::k_syrk_tc<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  tc::PSMEM_BYTES));
-    JMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    attr_dev = dev;
-  }
+  JMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  JMG_TRY(ensure_smem(tc::k_syrk_tc<KIND>, tc::PSMEM_BYTES));
   const int TI = cdiv(m, tc::BM), TJ = cdiv(ncols, tc::BN);
   const long long ntiles = (long long)TJ * (TJ + 1) / 2 + (long long)(TI - TJ) * TJ;
   const int grid = (int)std::min<long long>(ntiles, max_ctas > 0 ? std::min(max_ctas, nsm) : nsm);
   tc::k_syrk_tc<KIND><<<grid, tc::PTHREADS, tc::PSMEM_BYTES, s>>>(
-      ma, mb, C, ldc, m, ncols, kext, ab_fmt, (int)ntiles, TJ, exps, err);
+      ma, mb, C, ldc, m, ncols, kext, ab_fmt, (int)ntiles, TJ, exps, err, g_wait_ns, hold);
   return launched();
 }
 
 int launch_syrk_tc(int m, int ncols, int kext, const void* PA, const void* PB, int ldp, int prec,
-                   float* C, int ldc, int* err, cudaStream_t s, int max_ctas) {
+                   float* C, int ldc, int* err, cudaStream_t s, int max_ctas, int hold) {
   if (m <= 0 || ncols <= 0 || kext <= 0) return JMG_OK;
   if (ncols > m) return JMG_ERR_UNSUPPORTED;
   if (kext % tc::BK || ldp % 64 || ldp < kext) return JMG_ERR_ALIGN;
@@ -324,7 +324,7 @@ int launch_syrk_tc(int m, int ncols, int kext, const void* PA, const void* PB, i
   JMG_TRY(make_map(&ma, PA, m, kext, ldp, 2, dt));
   JMG_TRY(make_map(&mb, PB, m, kext, ldp, 2, dt));
   return syrk_persistent<0>(m, ncols, kext, ma, mb, prec == JMG_PREC_BF16 ? 1 : 0, nullptr, C, ldc,
-                            err, s, max_ctas);
+                            err, s, max_ctas, hold);
 }
 
 int launch_syrk_fp8(int m, int ncols, int kext, const void* Q, int ldq, const signed char* e,

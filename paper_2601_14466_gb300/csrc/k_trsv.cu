@@ -36,7 +36,6 @@ constexpr int CT = 256;   // compute threads
 constexpr int LAG = 3;    // blocks the leader multiplies itself: d-1 .. d-LAG+1
 constexpr int KCH = 2;    // finished blocks a helper multiplies per step (at most)
 constexpr int RING = 4;   // helper: blocks of L in flight or in use (KCH + 2)
-constexpr uint64_t WAIT_NS = 2000000000ull;
 
 // right-hand sides per group (all of them, up to 64, for FP32; 16 for FP64),
 // the register tile of the products (TM rows x TN columns per thread), and the
@@ -148,17 +147,18 @@ struct Vec<double, 1> {
   JMG_DEV static void load(const double* p, double (&v)[1]) { v[0] = *p; }
 };
 
-// Bounded spin of thread 0 until *p > d (acquire).  On expiry, or when another
-// CTA raised the error word, flags the abort: the solve is then incomplete.
+// Bounded spin of thread 0 until *p > d (acquire).  On expiry (limit_ns of
+// %globaltimer), or when another CTA raised the error word, flags the abort:
+// the solve is then incomplete.
 template <typename T>
-JMG_DEV void wait_gt(const int* p, int d, int* err, int* info, Smem<T>& S) {
+JMG_DEV void wait_gt(const int* p, int d, int* err, int* info, Smem<T>& S, uint64_t limit_ns) {
   int have = ld_acquire(p);
   if (have <= d) {
     const uint64_t t0 = globaltimer_ns();
     while ((have = ld_acquire(p)) <= d) {
-      if (globaltimer_ns() - t0 > WAIT_NS || *(volatile int*)err) {
+      if (globaltimer_ns() - t0 > limit_ns || *(volatile int*)err) {
         S.abort = 1;
-        atomicExch(err, 1);
+        atomicExch(err, JMG_ERR_TIMEOUT);
         if (info) atomicCAS(info, 0, -1);
         break;
       }
@@ -208,12 +208,14 @@ template <typename T>
 __global__ void __launch_bounds__(trsv::TH, 2)
     k_trsv_persist(int n, int nrhs, const T* __restrict__ L, int lda, T* __restrict__ B, int ldb,
                    int trans, int g0, int* __restrict__ tickets, int* __restrict__ done,
-                   int* __restrict__ pflag, int* __restrict__ err, int* __restrict__ info) {
+                   int* __restrict__ pflag, int* __restrict__ err, int* __restrict__ info,
+                   unsigned long long wait_ns, int tkt0) {
   using namespace trsv;
   constexpr int NR = Cfg<T>::NR, TM = Cfg<T>::TM, TN = Cfg<T>::TN, PADL = Cfg<T>::PADL;
   constexpr int RG = NBK / TM;  // row groups; column groups = TH / RG
   static_assert(RG * (NR / TN) == CT, "thread tile does not cover the block");
   if (info && *(volatile int*)info != 0) return;  // no factor: leave B alone
+  if (*(volatile int*)err != 0) return;           // the other direction gave up
   extern __shared__ __align__(16) unsigned char sm_raw_trsv[];
   Smem<T>& S = *reinterpret_cast<Smem<T>*>(sm_raw_trsv);
   const int nblk = cdiv_dev(n, NBK);
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(trsv::TH, 2)
   auto blk = [&](int d) { return trans ? nblk - 1 - d : d; };
 
   if (t == 0) {
-    S.ticket = atomicAdd(&tickets[grp], 1);
+    S.ticket = atomicAdd(&tickets[grp], 1) + tkt0;
     S.abort = 0;
   }
   __syncthreads();
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(trsv::TH, 2)
       const int lane = t - CT - 32;
       auto fetch = [&](int d) -> bool {  // P_d -> Pb[d & 1]; false on abort
         if (d >= LAG) {
-          if (lane == 0) wait_gt(&pf[d], 0, err, info, S);
+          if (lane == 0) wait_gt(&pf[d], 0, err, info, S, wait_ns);
           __syncwarp();
           if (ld_shared_volatile(&S.abort)) return false;
         }
@@ -406,7 +408,7 @@ __global__ void __launch_bounds__(trsv::TH, 2)
     int pfd = 0;  // blocks of L issued
     for (; pfd < min(ndep, RING - KCH); ++pfd) issue_L(pfd);
     for (int j = 0; j < ndep;) {
-      if (t == 0) wait_gt(cnt, j, err, info, S);
+      if (t == 0) wait_gt(cnt, j, err, info, S, wait_ns);
       __syncthreads();
       if (S.abort) break;
       const int ready = min(min(S.ready, ndep), j + KCH);
@@ -453,38 +455,36 @@ __global__ void __launch_bounds__(trsv::TH, 2)
     if (t == 0) {
       __threadfence();
       st_release(&pf[d], 1);
-      S.ticket = atomicAdd(&tickets[grp], 1);
+      S.ticket = atomicAdd(&tickets[grp], 1) + tkt0;
     }
     __syncthreads();
   }
 }
 
 size_t trsv_sync_ints(int n, int nrhs) {
-  // per group of right-hand sides (sized for the smaller, FP64, groups of 16):
-  // a ticket counter, a counter of finished blocks and one flag per block
-  // (P_d ready); then the error word
+  // the error word first; then per group of right-hand sides (sized for the
+  // smaller, FP64, groups of 16): a ticket counter, a counter of finished
+  // blocks and one flag per block (P_d ready)
   const int groups = cdiv(std::max(nrhs, 1), 16);
-  return (size_t)groups * (2 + cdiv(std::max(n, 1), trsv::NBK)) + 1;
+  return 1 + (size_t)groups * (2 + cdiv(std::max(n, 1), trsv::NBK));
 }
 
 template <typename T>
 int launch_trsv_persist(int n, int nrhs, const T* L, int lda, T* B, int ldb, int trans,
-                        int* sync, int* info, cudaStream_t s) {
+                        int* sync, int* info, cudaStream_t s, int tkt0) {
   if (n <= 0 || nrhs <= 0) return JMG_OK;
   const int groups = cdiv(nrhs, trsv::Cfg<T>::NR), nblk = cdiv(n, trsv::NBK);
-  int* tickets = sync;
-  int* done = sync + groups;
+  int* err = sync;
+  int* tickets = sync + 1;
+  int* done = tickets + groups;
   int* pflag = done + groups;
-  int* err = pflag + (size_t)groups * nblk;
-  JMG_CUDA(cudaMemsetAsync(sync, 0, sizeof(int) * trsv_sync_ints(n, nrhs), s));
+  // the forward solve clears the error word with the rest; the backward solve
+  // keeps it, so that it returns at once after a forward solve that gave up
+  JMG_CUDA(cudaMemsetAsync(sync + (trans ? 1 : 0), 0,
+                           sizeof(int) * (trsv_sync_ints(n, nrhs) - (trans ? 1 : 0)), s));
   const size_t smem = sizeof(trsv::Smem<T>);
   auto k = k_trsv_persist<T>;
-  static int done_attr[2] = {0, 0};
-  const int which = sizeof(T) == 8;
-  if (!done_attr[which]) {
-    JMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    done_attr[which] = 1;
-  }
+  JMG_TRY(ensure_smem(k, (int)smem));
   // a leader plus one helper per block when they all fit; the tickets keep the
   // dependency order either way.  A leader waits for its helpers, so every
   // launch keeps all of its CTAs resident: groups go in batches of at most
@@ -501,14 +501,14 @@ int launch_trsv_persist(int n, int nrhs, const T* L, int lda, T* B, int ldb, int
     const int gn = std::min(batch, groups - g0);
     const int gx = std::max(2, std::min(want, slots / gn));
     k<<<dim3(gx, gn), trsv::TH, smem, s>>>(n, nrhs, L, lda, B, ldb, trans, g0, tickets, done,
-                                           pflag, err, info);
+                                           pflag, err, info, g_wait_ns, tkt0);
     JMG_TRY(launched());
   }
   return JMG_OK;
 }
 template int launch_trsv_persist<float>(int, int, const float*, int, float*, int, int, int*,
-                                        int*, cudaStream_t);
+                                        int*, cudaStream_t, int);
 template int launch_trsv_persist<double>(int, int, const double*, int, double*, int, int, int*,
-                                         int*, cudaStream_t);
+                                         int*, cudaStream_t, int);
 
 }  // namespace jmg

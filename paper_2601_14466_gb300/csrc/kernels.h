@@ -45,11 +45,16 @@ int posv_small_batched(int n, int nrhs, int batch, T* A, int lda, long long sA, 
 
 // One-launch blocked solve with the whole factor, in place on B:
 // trans == 0: L Y = B;  trans == 1: L^T X = B.  `sync` holds
-// trsv_sync_ints(n, nrhs) ints of scratch (tickets, finished-block counters, per-block flags, error word).
+// trsv_sync_ints(n, nrhs) ints of scratch: sync[0] is the error word (0, or
+// JMG_ERR_TIMEOUT once a device-side wait ran out; the forward solve clears it,
+// the backward solve keeps it and does nothing if it is set), then tickets,
+// finished-block counters and per-block flags.  tkt0 != 0 is a test hook: every
+// ticket is offset by tkt0, so no CTA leads and the helpers' bounded waits run
+// out (g_wait_ns).
 size_t trsv_sync_ints(int n, int nrhs);
 template <typename T>
 int launch_trsv_persist(int n, int nrhs, const T* L, int lda, T* B, int ldb, int trans, int* sync,
-                        int* info, cudaStream_t s);
+                        int* info, cudaStream_t s, int tkt0 = 0);
 // (L L^T) X = B: forward then backward with launch_trsv_persist.
 template <typename T>
 int solve_llt(int n, int nrhs, const T* L, int lda, T* B, int ldb, int* sync, int* info,
@@ -139,8 +144,10 @@ int launch_sym_grad(int n, int nrhs, const double* Bb, int ldb, const double* X,
 // C (m x ncols, lower trapezoid: rows >= columns) -= PA PB^T, PA/PB: m x kext
 // row-major 16-bit words; ncols <= m.
 // max_ctas > 0 caps the persistent grid (to leave SMs free for concurrent work).
+// hold != 0 is a test hook: the TMA producer stays idle, so the kernel's first
+// bounded wait runs out (g_wait_ns) and it returns through its abort path.
 int launch_syrk_tc(int m, int ncols, int kext, const void* PA, const void* PB, int ldp, int prec,
-                   float* C, int ldc, int* err, cudaStream_t s, int max_ctas = 0);
+                   float* C, int ldc, int* err, cudaStream_t s, int max_ctas = 0, int hold = 0);
 // FP8 e4m3 variant: Q (m x kext bytes, row-major, ldq), C -= 2^-(e[ti]+e[tj]) Q_ti Q_tj^T
 int launch_syrk_fp8(int m, int ncols, int kext, const void* Q, int ldq, const signed char* e,
                     float* C, int ldc, int* err, cudaStream_t s, int max_ctas = 0);

@@ -10,8 +10,6 @@
 namespace jmg {
 namespace tc {
 
-constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s per wait: far above any legal wait
-
 JMG_DEV void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
                : "memory");
@@ -34,13 +32,14 @@ JMG_DEV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: true when the phase with `parity` completed, false on timeout.
-JMG_DEV bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait: true when the phase with `parity` completed, false once
+// `limit_ns` nanoseconds (%globaltimer) have passed without it.
+JMG_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (globaltimer_ns() - t0 > WAIT_NS) return false;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
   }
 }
 JMG_DEV void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {

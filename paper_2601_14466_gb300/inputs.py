@@ -62,7 +62,9 @@ def gram_shift(n: int, shift: float, seed: int = 0, device="cpu", fp32_product: 
     return A.contiguous()
 
 
-def q_lambda(n: int, kappa: float, seed: int = 0, device="cpu") -> torch.Tensor:
+def q_factor(n: int, seed: int = 0, device="cpu") -> torch.Tensor:
+    """Q of the Householder QR of an i.i.d. N(0,1) n x n matrix, with the signs
+    fixed so that diag(R) > 0 (a Haar-distributed orthogonal matrix)."""
     g = _gen(seed, device)
     G = torch.randn((n, n), generator=g, dtype=torch.float64, device=device)
     Q, R = torch.linalg.qr(G)
@@ -70,12 +72,35 @@ def q_lambda(n: int, kappa: float, seed: int = 0, device="cpu") -> torch.Tensor:
     s = torch.sign(torch.diagonal(R))
     s[s == 0] = 1.0
     Q.mul_(s.unsqueeze(0))
-    del R
-    lam = log_spaced(n, kappa, device=device)
-    A = (Q * lam.unsqueeze(0)) @ Q.t()
-    del Q
+    return Q
+
+
+def from_q(Q: torch.Tensor, kappa: float) -> torch.Tensor:
+    """A = Q diag(lambda) Q^T with lambda log-spaced in [1, kappa], symmetrised.
+    Several condition numbers can share one (expensive) Q."""
+    n = Q.shape[0]
+    lam = log_spaced(n, kappa, device=Q.device)
+    QL = Q * lam.unsqueeze(0)
+    # the product block by block, lower blocks only, mirrored (A is symmetric;
+    # this skips ~40% of the FP64 multiply work of a full product)
+    A = torch.empty((n, n), dtype=Q.dtype, device=Q.device)
+    nb = 8
+    cuts = [n * k // nb for k in range(nb + 1)]
+    for bi in range(nb):
+        r0, r1 = cuts[bi], cuts[bi + 1]
+        for bj in range(bi + 1):
+            c0, c1 = cuts[bj], cuts[bj + 1]
+            blk = QL[r0:r1] @ Q[c0:c1].t()
+            A[r0:r1, c0:c1] = blk
+            if bj < bi:
+                A[c0:c1, r0:r1] = blk.t()
+    del QL
     A = 0.5 * (A + A.t())
     return A.contiguous()
+
+
+def q_lambda(n: int, kappa: float, seed: int = 0, device="cpu") -> torch.Tensor:
+    return from_q(q_factor(n, seed, device), kappa)
 
 
 def log_spaced(n: int, kappa: float, device="cpu") -> torch.Tensor:
@@ -128,6 +153,21 @@ def integer_factor(n: int, seed: int = 0, max_abs: int = 8, max_exp: int = 3):
     A = L @ L.t()  # exact in int64
     assert int(A.abs().max()) < 2 ** 52
     return L.to(torch.float64), A.to(torch.float64)
+
+
+def lower_factor(n: int, seed: int = 0, device="cpu") -> torch.Tensor:
+    """A well-conditioned lower-triangular factor for solve-only tests (no
+    factorisation needed): strictly lower entries i.i.d. N(0, 1/n), diagonal
+    2 + U[0, 1].  Row i's off-diagonal part has 2-norm about sqrt(i/n) <= 1,
+    so forward and back substitution keep |y| of the order of |b| and every
+    block product changes the result at O(1).  Column-major, upper triangle 0."""
+    g = _gen(seed, device)
+    L = torch.randn((n, n), generator=g, dtype=torch.float64, device=device)
+    L.mul_(n ** -0.5)
+    L = torch.tril(L, -1)
+    d = torch.rand(n, generator=g, dtype=torch.float64, device=device)
+    L.diagonal().copy_(2.0 + d)
+    return L.t().contiguous().t()
 
 
 def nominal_flops(n: int, nrhs: int) -> float:

@@ -92,6 +92,11 @@ _SIGS = {
     "jmg_dev_norm_inf": (_I, [_I, _P, _I, _P, _P, _SZ, _P]),
     "jmg_dev_probe": (_I, [_I, _I, _I, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "jmg_dev_launch_count": (ctypes.c_longlong, []),
+    "jmg_dev_set_wait_limit_ns": (ctypes.c_ulonglong, [ctypes.c_ulonglong]),
+    "jmg_dev_trsv_leaderless": (_I, [_I, _I, _P, _I, _P, _I, _I, _P, _P, _P]),
+    "jmg_dev_syrk_tc_idle_producer": (_I, [_I, _I, _I, _P, _P, _I, _I, _P, _I, _P, _P]),
+    "jmg_dev_quant_fp8": (_I, [_I, _I, _P, _I, _P, _I, _P, _P]),
+    "jmg_potrs_static_status": (_I, [ctypes.POINTER(_I), _P]),
     "jmg_posv_batched": (_I, [_I, _I, _I, _P, _I, ctypes.c_longlong, _P, _I, ctypes.c_longlong, _I,
                               _P, _P]),
 }
@@ -520,3 +525,25 @@ def probe(kind: int, blocks: int, iters: int, device="cuda"):
 
 def launch_count() -> int:
     return int(load().jmg_dev_launch_count())
+
+
+def set_wait_limit_ns(ns: int) -> int:
+    """Set the time limit of every device-side wait (nanoseconds); returns the
+    previous limit.  0 only queries."""
+    return int(load().jmg_dev_set_wait_limit_ns(int(ns)))
+
+
+def quant_fp8(L21: torch.Tensor):
+    """The mixed factorisation's FP8 quantiser on its own: L21 (m x kb FP32,
+    column-major) -> (Q, e): Q (m, kb) e4m3 bytes row-major (uint8), e the int8
+    power-of-two exponent of each 128-row tile."""
+    _need_cuda(L21)
+    if L21.dtype != torch.float32:
+        raise TypeError("quant_fp8: L21 must be float32")
+    m, kb = L21.shape
+    pl, ldw = _colmajor(L21, "L21")
+    Q = torch.zeros((m, kb), dtype=torch.uint8, device=L21.device)
+    e = torch.zeros(max((m + 127) // 128, 1), dtype=torch.int8, device=L21.device)
+    _chk(load().jmg_dev_quant_fp8(m, kb, pl, ldw, Q.data_ptr(), kb, e.data_ptr(),
+                                  _stream(L21.device)), "jmg_dev_quant_fp8")
+    return Q, e[:(m + 127) // 128]

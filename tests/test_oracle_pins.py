@@ -272,9 +272,35 @@ def pin_grad_library(o):
     assert np.abs(Bbar - Bt.grad.numpy()).max() <= 1e-12 * max(1.0, np.abs(Bbar).max())
 
 
+def pin_bwd_err_rows_bit_identical(o):
+    # the cache-friendly sweep computes every residual entry and row sum with
+    # the same operations in the same order as the plain definition, so it must
+    # agree bit for bit (ragged row blocks, one and several right-hand sides, a
+    # NaN, a zero right-hand side)
+    for n, nrhs, seed in [(1, 1, 0), (31, 1, 1), (33, 3, 2), (100, 7, 3), (257, 2, 4)]:
+        A = inputs.q_lambda(n, 1e6, seed) if n > 1 else np.array([[2.0]])
+        A = np.asarray(A)
+        X = np.random.default_rng(seed).uniform(-1, 1, (n, nrhs))
+        B = np.asfortranarray(_full(A) @ X + 1e-9 * np.random.default_rng(seed + 9).standard_normal((n, nrhs)))
+        if nrhs > 2:
+            B[:, 1] = 0.0
+            X[:, 1] = 0.0
+        w1, e1 = o.bwd_err(A, X, B)
+        w2, e2 = o.bwd_err_rows(A, X, B)
+        assert w1 == w2 and np.array_equal(e1, e2), (n, nrhs)
+    A = _spd(40, 5)
+    X = np.ones((40, 2))
+    X[7, 1] = np.nan
+    B = _full(A) @ np.ones((40, 2))
+    w1, e1 = o.bwd_err(A, X, B)
+    w2, e2 = o.bwd_err_rows(A, X, B)
+    assert np.isnan(w1) and np.isnan(w2) and e1[0] == e2[0] and np.isnan(e2[1])
+
+
 PINS = [pin_textbook, pin_integer_factor, pin_diag_closed_form, pin_ge_agrees, pin_ge_pivots,
         pin_known_solution, pin_scipy_cholesky, pin_potrs_residual, pin_dot2_exact,
-        pin_bwd_err_formula, pin_not_spd, pin_logdet_library, pin_grad_fd, pin_grad_library]
+        pin_bwd_err_formula, pin_not_spd, pin_logdet_library, pin_grad_fd, pin_grad_library,
+        pin_bwd_err_rows_bit_identical]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=lambda p: p.__name__)
@@ -330,6 +356,13 @@ MUTANTS = {
     "grad_uses_b": ("Bbar[(size_t)c * n + i] = AT(Xbar, i, c, ldxb);",
                     "Bbar[(size_t)c * n + i] = AT(B, i, c, ldb);"),
     "logdet_no_log": ("s += log(AT(L, i, i, lda));", "s += AT(L, i, i, lda);"),
+    "rows_drop_prod_err": ("comp[(size_t)ii * nr + c] += es + ep;",
+                           "comp[(size_t)ii * nr + c] += es;"),
+    "rows_norm_no_abs": ("asum[ii] += fabs(a);", "asum[ii] += a;"),
+    "rows_lower_only": ("const double a = sym_at(A, lda, i0 + ii, j);",
+                        "const double a = j <= i0 + ii ? sym_at(A, lda, i0 + ii, j) : 0.0;"),
+    "rows_skip_tail": ("const int ib = n - i0 < ORACLE_ROWS ? n - i0 : ORACLE_ROWS;",
+                       "const int ib = n - i0 < ORACLE_ROWS ? n - i0 - 1 : ORACLE_ROWS;"),
 }
 
 
