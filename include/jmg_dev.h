@@ -114,6 +114,19 @@ int jmg_dev_syrk_tc_idle_producer(int m, int ncols, int kext, const void* PA, co
                                   int ldp, int prec, float* C, int ldc, int* err, void* stream);
 
 /*
+ * The block-inverse triangular solves of the mixed path on a caller's FP32
+ * factor: (L L^T) X = B in place on B (FP32, n x nrhs, column-major).  The
+ * call copies lower(L) and B into `work` (the solves need W's upper triangle
+ * and 128-byte aligned leading dimensions), forms the inverses of the 128 x 128
+ * diagonal blocks and the chain's coupling blocks, runs the forward and the
+ * backward solve and copies X back into B.  work: jmg_dev_sv_workspace(n, nrhs)
+ * bytes, 256-byte aligned.  Asynchronous.
+ */
+size_t jmg_dev_sv_workspace(int n, int nrhs);
+int jmg_dev_sv_potrs(int n, int nrhs, const float* L, int lda, float* B, int ldb, void* work,
+                     size_t lwork, void* stream);
+
+/*
  * The FP8 quantiser of the mixed factorisation on its own: the FP32 panel
  * L21 (m x kb, column-major, ldw) becomes Q (m x kb e4m3 bytes, row-major, ldq
  * >= kb) with one exponent per 128-row tile t:

@@ -26,9 +26,9 @@ struct Plan {
   size_t off_W = 0, off_PA = 0, off_PB = 0, off_X = 0, off_R = 0, off_D = 0, off_part = 0,
          off_colmax = 0, off_eta = 0, off_anorm = 0, off_rowsum = 0, off_ints = 0, off_Z = 0,
          off_P = 0, off_Q = 0, off_scal = 0, off_sync = 0, off_exp = 0, off_ozrow = 0,
-         off_ozA = 0, off_ozX = 0, total = 0;
+         off_ozA = 0, off_ozX = 0, off_SV = 0, total = 0;
   bool split = false;
-  int ldw = 0, ldp = 0, kext = 0, splits = 1;
+  int ldw = 0, ldp = 0, kext = 0, splits = 1, ldd = 0;
 };
 
 static void opts_or_default(const jmg_options* in, jmg_options* out) {
@@ -54,12 +54,14 @@ static Plan plan_posv_mixed(int n, int nrhs, const jmg_options& o) {
   };
   const size_t N = (size_t)n, R = (size_t)(nrhs > 0 ? nrhs : 1);
   p.ldw = (int)round_up(N > 0 ? N : 1, 32);
+  p.ldd = p.ldw;  // the FP32 right-hand sides of the preconditioner solves
   p.kext = o.prec == JMG_PREC_FP8 ? o.nb : o.nb * split_pairs(o.words);
   p.ldp = (int)round_up((size_t)p.kext, 64);
   p.splits = residual_splits(n, nrhs > 0 ? nrhs : 1);
   // the factor and what a refine-only call (reuse_factor) needs come first, at
   // offsets that do not depend on nrhs
   p.off_W = take(sizeof(float) * (size_t)p.ldw * N);
+  p.off_SV = take(sv_image_bytes(n));  // inverses and coupling blocks of the solves
   p.off_anorm = take(sizeof(double) * 2);  // [0] ||A||_inf, [1] shift of the factor
   p.off_ints = take(sizeof(int) * 8);
   p.split = o.resid != 1;  // tensor-core split products (auto or explicit)
@@ -72,7 +74,7 @@ static Plan plan_posv_mixed(int n, int nrhs, const jmg_options& o) {
   p.off_PB = take(2 * N * p.ldp);
   p.off_X = take(sizeof(double) * N * R);
   p.off_R = take(sizeof(double) * N * R);
-  p.off_D = take(sizeof(float) * N * R);
+  p.off_D = take(sizeof(float) * (size_t)p.ldd * R);
   if (p.split) {
     p.off_ozX = take(oz_x_bytes(n, nrhs > 0 ? nrhs : 1));
     p.splits = std::max(p.splits, oz_splits_used(n, nrhs > 0 ? nrhs : 1));
@@ -85,7 +87,8 @@ static Plan plan_posv_mixed(int n, int nrhs, const jmg_options& o) {
   p.off_P = take(sizeof(double) * N * R);
   p.off_Q = take(sizeof(double) * N * R);
   p.off_scal = take(sizeof(double) * 8 * R);
-  p.off_sync = take(sizeof(int) * trsv_sync_ints(n, nrhs > 0 ? nrhs : 1));
+  p.off_sync = take(sizeof(int) * std::max(trsv_sync_ints(n, nrhs > 0 ? nrhs : 1),
+                                            sv_sync_ints(n, nrhs > 0 ? nrhs : 1)));
   p.total = off;
   return p;
 }
@@ -197,7 +200,9 @@ static int factor_mixed(int n, float* W, int ldw, const jmg_options& o, const Pl
     }
     JMG_CUDA(cudaStreamWaitEvent(s, side.diag, 0));
   }
-  return JMG_OK;
+  // the solves' images: inverses of the diagonal blocks, coupling blocks, and
+  // L mirrored into the upper triangle of W
+  return sv_prepare(n, W, ldw, at<float>(work, p.off_SV), s);
 }
 
 // column max of |B| into colmax_r and R = B (start of refinement from X = 0)
@@ -230,14 +235,14 @@ static int sync_read(void* host, const void* dev, size_t bytes, cudaStream_t s) 
 
 // M^{-1} R in FP32 with per-column scaling, added to X (FP64): X += s * (L L^T)^{-1} (R / s)
 // `status` is a device int set to -1 if a device-side wait of the solve ran out.
-static int precond_update(int n, int nrhs, const float* W, int ldw, const double* R,
-                          const double* colmax_r, float* D, double* X, int* sync, int* status,
-                          cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
-  JMG_TRY(launch_scale_to_f32(n, nrhs, R, n, colmax_r, D, n, s));
+static int precond_update(int n, int nrhs, const float* W, int ldw, const float* SV,
+                          const double* R, const double* colmax_r, float* D, int ldd, double* X,
+                          int* sync, int* status, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  JMG_TRY(launch_scale_to_f32(n, nrhs, R, n, colmax_r, D, ldd, s));
   if (e0) JMG_CUDA(cudaEventRecord(e0, s));
-  JMG_TRY(solve_llt<float>(n, nrhs, W, ldw, D, n, sync, status, s));
+  JMG_TRY(sv_solve_llt(n, nrhs, W, ldw, SV, D, ldd, sync, status, s));
   if (e1) JMG_CUDA(cudaEventRecord(e1, s));
-  JMG_TRY(launch_axpy_f32(n, nrhs, D, n, colmax_r, X, n, s));
+  JMG_TRY(launch_axpy_f32(n, nrhs, D, ldd, colmax_r, X, n, s));
   return JMG_OK;
 }
 
@@ -310,14 +315,15 @@ static int true_residual(MixedCtx& c) {
 
 // Z = M^{-1} R with the FP32 factor (per-column scaling by ||r_c||)
 static int precond_to(MixedCtx& c, double* Zout) {
-  JMG_TRY(launch_scale_to_f32(c.n, c.nrhs, c.R, c.n, c.colmax, c.D, c.n, c.s));
+  JMG_TRY(launch_scale_to_f32(c.n, c.nrhs, c.R, c.n, c.colmax, c.D, c.p->ldd, c.s));
   if (c.ev[2]) JMG_CUDA(cudaEventRecord(c.ev[2], c.s));
-  JMG_TRY(solve_llt<float>(c.n, c.nrhs, c.W, c.p->ldw, c.D, c.n, c.sync, &c.ints[2], c.s));
+  JMG_TRY(sv_solve_llt(c.n, c.nrhs, c.W, c.p->ldw, at<float>(c.work, c.p->off_SV), c.D, c.p->ldd,
+                       c.sync, &c.ints[2], c.s));
   if (c.ev[3]) {
     JMG_CUDA(cudaEventRecord(c.ev[3], c.s));
     c.solve_pending = true;
   }
-  return launch_scale_from_f32(c.n, c.nrhs, c.D, c.colmax, Zout, c.s);
+  return launch_scale_from_f32(c.n, c.nrhs, c.D, c.p->ldd, c.colmax, Zout, c.s);
 }
 
 // Preconditioned CG on A X = B from the current X and its true residual R,
@@ -504,8 +510,8 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
       k_copy_colmax<<<grid, 256, 0, s>>>(n, B, ldb, c.R, c.colmax);
       JMG_TRY(launched());
     }
-    JMG_TRY(precond_update(n, nrhs, c.W, p.ldw, c.R, c.colmax, c.D, c.X, c.sync, &c.ints[2], s,
-                           c.ev[2], c.ev[3]));
+    JMG_TRY(precond_update(n, nrhs, c.W, p.ldw, at<float>(work, p.off_SV), c.R, c.colmax, c.D,
+                           p.ldd, c.X, c.sync, &c.ints[2], s, c.ev[2], c.ev[3]));
     c.solve_pending = c.ev[3] != nullptr;
     const double t2 = now_ms();
     S.t_solve_ms += t2 - t1;
@@ -536,8 +542,8 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
       }
       prev = c.eh[0];
       if (!use_pcg) {
-        JMG_TRY(precond_update(n, nrhs, c.W, p.ldw, c.R, c.colmax, c.D, c.X, c.sync, &c.ints[2],
-                               s, c.ev[2], c.ev[3]));
+        JMG_TRY(precond_update(n, nrhs, c.W, p.ldw, at<float>(work, p.off_SV), c.R, c.colmax,
+                               c.D, p.ldd, c.X, c.sync, &c.ints[2], s, c.ev[2], c.ev[3]));
         c.solve_pending = c.ev[3] != nullptr;
         S.iters++;
         continue;
@@ -953,6 +959,62 @@ int jmg_dev_norm_inf(int n, const double* A, int lda, double* out, void* work, s
 }
 
 long long jmg_dev_launch_count(void) { return g_launches; }
+
+// layout of jmg_dev_sv_potrs's workspace: W (ldw x n), D (ldw x nrhs), images, sync
+struct SvDevLayout {
+  size_t W, D, SV, sync, total;
+  int ldw;
+};
+static SvDevLayout sv_dev_layout(int n, int nrhs) {
+  SvDevLayout L;
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    size_t at = off;
+    off = round_up(off + b, 256);
+    return at;
+  };
+  L.ldw = (int)round_up((size_t)std::max(n, 1), 32);
+  L.W = take(sizeof(float) * (size_t)L.ldw * std::max(n, 1));
+  L.D = take(sizeof(float) * (size_t)L.ldw * std::max(nrhs, 1));
+  L.SV = take(sv_image_bytes(n));
+  L.sync = take(sizeof(int) * sv_sync_ints(n, nrhs));
+  L.total = off;
+  return L;
+}
+
+size_t jmg_dev_sv_workspace(int n, int nrhs) {
+  if (n <= 0 || nrhs <= 0) return 0;
+  return sv_dev_layout(n, nrhs).total;
+}
+
+int jmg_dev_sv_potrs(int n, int nrhs, const float* L, int lda, float* B, int ldb, void* work,
+                     size_t lwork, void* stream) {
+  if (n < 0) return -1;
+  if (nrhs < 0) return -2;
+  if (lda < std::max(1, n)) return -4;
+  if (ldb < std::max(1, n)) return -6;
+  if (n == 0 || nrhs == 0) return JMG_OK;
+  if (!L) return -3;
+  if (!B) return -5;
+  const SvDevLayout Lo = sv_dev_layout(n, nrhs);
+  if (!work || lwork < Lo.total) return JMG_ERR_WORKSPACE;
+  if (reinterpret_cast<uintptr_t>(work) & 255) return JMG_ERR_ALIGN;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* w = static_cast<char*>(work);
+  float* W = reinterpret_cast<float*>(w + Lo.W);
+  float* D = reinterpret_cast<float*>(w + Lo.D);
+  float* SV = reinterpret_cast<float*>(w + Lo.SV);
+  int* sync = reinterpret_cast<int*>(w + Lo.sync);
+  JMG_CUDA(cudaMemcpy2DAsync(W, sizeof(float) * Lo.ldw, L, sizeof(float) * lda, sizeof(float) * n,
+                             n, cudaMemcpyDeviceToDevice, s));
+  JMG_CUDA(cudaMemcpy2DAsync(D, sizeof(float) * Lo.ldw, B, sizeof(float) * ldb, sizeof(float) * n,
+                             nrhs, cudaMemcpyDeviceToDevice, s));
+  JMG_TRY(sv_prepare(n, W, Lo.ldw, SV, s));
+  JMG_TRY(sv_solve_llt(n, nrhs, W, Lo.ldw, SV, D, Lo.ldw, sync, nullptr, s));
+  JMG_CUDA(cudaMemcpy2DAsync(B, sizeof(float) * ldb, D, sizeof(float) * Lo.ldw, sizeof(float) * n,
+                             nrhs, cudaMemcpyDeviceToDevice, s));
+  return JMG_OK;
+}
 
 unsigned long long jmg_dev_set_wait_limit_ns(unsigned long long ns) {
   const unsigned long long old = g_wait_ns;

@@ -1186,19 +1186,19 @@ int launch_pcg_dir(int n, int nrhs, const double* Z, double* P, const double* rz
 }
 
 // Z = scale_c * D32 (FP64 from the FP32 preconditioner output)
-__global__ void k_scale_from_f32(int n, const float* __restrict__ D, const double* __restrict__ colmax_r,
-                                 double* __restrict__ Z) {
+__global__ void k_scale_from_f32(int n, const float* __restrict__ D, int ldd,
+                                 const double* __restrict__ colmax_r, double* __restrict__ Z) {
   const int c = blockIdx.y;
   double sc = colmax_r[c];
   if (!(sc > 0.0 && isfinite(sc))) sc = 1.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    Z[(size_t)c * n + i] = sc * (double)D[(size_t)c * n + i];
+    Z[(size_t)c * n + i] = sc * (double)D[(size_t)c * ldd + i];
 }
 
-int launch_scale_from_f32(int n, int nrhs, const float* D, const double* colmax_r, double* Z,
-                          cudaStream_t s) {
+int launch_scale_from_f32(int n, int nrhs, const float* D, int ldd, const double* colmax_r,
+                          double* Z, cudaStream_t s) {
   dim3 grid(std::min(cdiv(n, 256), 64), nrhs);
-  k_scale_from_f32<<<grid, 256, 0, s>>>(n, D, colmax_r, Z);
+  k_scale_from_f32<<<grid, 256, 0, s>>>(n, D, ldd, colmax_r, Z);
   return launched();
 }
 

@@ -279,6 +279,21 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
+int make_tmap_2d(CUtensorMap* map, const void* base, unsigned long long inner,
+                 unsigned long long outer, unsigned long long ld_bytes, unsigned box_inner,
+                 unsigned box_outer, CUtensorMapDataType dt, CUtensorMapSwizzle sw) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return JMG_ERR_CUDA;
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  cuuint64_t strides[1] = {(cuuint64_t)ld_bytes};
+  cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? JMG_OK : JMG_ERR_CUDA;
+}
+
 // 2D map over a row-major rows x cols matrix (element size esize bytes), box
 // of 128 bytes x 128 rows, 128-byte swizzle.
 static int make_map(CUtensorMap* map, const void* base, int rows, int cols, int ld, int esize,

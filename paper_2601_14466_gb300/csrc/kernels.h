@@ -1,6 +1,8 @@
 // kernels.h -- internal launchers of the SPD solver's kernels (not exported).
 #pragma once
 
+#include <cuda.h>
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -132,13 +134,40 @@ int launch_pcg_step(int n, int nrhs, const double* P, const double* Q, const dou
                     cudaStream_t s);
 int launch_pcg_dir(int n, int nrhs, const double* Z, double* P, const double* rz_new,
                    const double* rz_old, cudaStream_t s);
-int launch_scale_from_f32(int n, int nrhs, const float* D, const double* colmax_r, double* Z,
-                          cudaStream_t s);
+int launch_scale_from_f32(int n, int nrhs, const float* D, int ldd, const double* colmax_r,
+                          double* Z, cudaStream_t s);
 int launch_diag_max(int n, const double* A, int lda, double* out, cudaStream_t s);
 
 // ---- adjoint (k_grad.cu): G = -(Bb X^T + X Bb^T)/2, full symmetric n x n
 int launch_sym_grad(int n, int nrhs, const double* Bb, int ldb, const double* X, int ldx, double* G,
                     int ldg, cudaStream_t s);
+
+// ---- block-inverse solves with the FP32 factor of the mixed path (k_solve.cu)
+// Bytes of the per-factorisation images (inverses of the diagonal blocks and the
+// chain's coupling matrices) and ints of solve scratch.
+size_t sv_image_bytes(int n);
+size_t sv_sync_ints(int n, int nrhs);
+// Once per factorisation of W (FP32, lower, ldw % 32 == 0, 16-byte aligned):
+// mirror the strictly lower blocks into the upper triangle of W and write the
+// images into SV (sv_image_bytes(n), 256-byte aligned).
+int sv_prepare(int n, float* W, int ldw, float* SV, cudaStream_t s);
+// trans == 0: L Y = D; trans == 1: L^T X = D, in place on D (FP32, n x nrhs,
+// ldd % 32 == 0).  sync: sv_sync_ints(n, nrhs) ints; sync[0] is the error word
+// (cleared by the forward solve, kept by the backward solve).  info: as
+// launch_trsv_persist (may be NULL).
+int sv_solve(int n, int nrhs, const float* W, int ldw, const float* SV, float* D, int ldd,
+             int trans, int* sync, int* info, cudaStream_t s);
+inline int sv_solve_llt(int n, int nrhs, const float* W, int ldw, const float* SV, float* D,
+                        int ldd, int* sync, int* info, cudaStream_t s) {
+  JMG_TRY(sv_solve(n, nrhs, W, ldw, SV, D, ldd, 0, sync, info, s));
+  return sv_solve(n, nrhs, W, ldw, SV, D, ldd, 1, sync, info, s);
+}
+
+// 2D tiled tensor map over a matrix with `inner` contiguous elements per line
+// (leading dimension ld_bytes), `outer` lines; box box_inner x box_outer.
+int make_tmap_2d(CUtensorMap* map, const void* base, unsigned long long inner,
+                 unsigned long long outer, unsigned long long ld_bytes, unsigned box_inner,
+                 unsigned box_outer, CUtensorMapDataType dt, CUtensorMapSwizzle sw);
 
 // ---- tensor-core trailing update (k_tc.cu)
 // C (m x ncols, lower trapezoid: rows >= columns) -= PA PB^T, PA/PB: m x kext

@@ -96,6 +96,8 @@ _SIGS = {
     "jmg_dev_trsv_leaderless": (_I, [_I, _I, _P, _I, _P, _I, _I, _P, _P, _P]),
     "jmg_dev_syrk_tc_idle_producer": (_I, [_I, _I, _I, _P, _P, _I, _I, _P, _I, _P, _P]),
     "jmg_dev_quant_fp8": (_I, [_I, _I, _P, _I, _P, _I, _P, _P]),
+    "jmg_dev_sv_workspace": (_SZ, [_I, _I]),
+    "jmg_dev_sv_potrs": (_I, [_I, _I, _P, _I, _P, _I, _P, _SZ, _P]),
     "jmg_potrs_static_status": (_I, [ctypes.POINTER(_I), _P]),
     "jmg_posv_batched": (_I, [_I, _I, _I, _P, _I, ctypes.c_longlong, _P, _I, ctypes.c_longlong, _I,
                               _P, _P]),
@@ -525,6 +527,22 @@ def probe(kind: int, blocks: int, iters: int, device="cuda"):
 
 def launch_count() -> int:
     return int(load().jmg_dev_launch_count())
+
+
+def sv_potrs_(L: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
+    """The mixed path's block-inverse solves on an FP32 factor: (L L^T) X = B in
+    place on B (both FP32, column-major); asynchronous."""
+    _need_cuda(L, B)
+    if L.dtype != torch.float32 or B.dtype != torch.float32:
+        raise TypeError("sv_potrs_: L and B must be float32")
+    pl, lda = _colmajor(L, "L")
+    pb, ldb = _colmajor(B, "B")
+    n, nrhs = L.shape[0], B.shape[1]
+    nbytes = int(load().jmg_dev_sv_workspace(n, nrhs))
+    work = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=L.device)
+    _chk(load().jmg_dev_sv_potrs(n, nrhs, pl, lda, pb, ldb, work.data_ptr(), work.numel(),
+                                 _stream(L.device)), "jmg_dev_sv_potrs")
+    return B
 
 
 def set_wait_limit_ns(ns: int) -> int:
