@@ -46,7 +46,7 @@ namespace sv {
 
 constexpr int BS = 128;            // block rows
 constexpr int LAG = 3;             // blocks the leader multiplies itself: d-1, d-2
-constexpr int CG = 16;             // right-hand sides per leader
+constexpr int CG = 8;              // right-hand sides per leader
 constexpr int NMAX = 64;           // right-hand sides per launch
 constexpr int TH = 352;            // 8 compute warps, producer, publisher, fetcher
 constexpr int NCOMP = 256;
@@ -58,8 +58,9 @@ constexpr int HSLOTS = 2;          // helper: tile ring
 // The compute warps split the k range of every product (each warp reads only
 // its part of a block, so shared memory is read about once per product) and
 // the columns; partial sums meet once per step (leader) or per block (helper).
-// Leader: 4 k-groups (one 32-wide slab each) x 2 column halves of 8.
-constexpr int L_KG = 4, L_CQ = 2, L_CT = CG / L_CQ;
+// Leader: L_KG k-groups of L_KLEN k each x L_CQ column groups of L_CT.
+constexpr int L_CQ = CG >= 16 ? 2 : 1, L_CT = CG / L_CQ, L_KG = 8 / L_CQ, L_KLEN = BS / L_KG;
+constexpr int L_SLAB_READERS = (32 / L_KLEN) * L_CQ;  // warps that read each slab
 // dynamic shared memory: helper = 2 x (64 KB tile + up to 32 KB of Y);
 // leader = 8 x 16 KB slabs + 2 P buffers + 3 Y buffers + 3 partial-sum
 // buffers (16 columns x 512 B each)
@@ -389,7 +390,7 @@ __global__ void __launch_bounds__(sv::TH, 1)
     if (t == 0) {
       for (int s = 0; s < LSLOTS; ++s) {
         tc::mbar_init(&sfull[s], 1);
-        tc::mbar_init(&sempty[s], L_CQ);  // the two warps of the slab's k-group
+        tc::mbar_init(&sempty[s], L_SLAB_READERS);
       }
       for (int s = 0; s < 2; ++s) {
         tc::mbar_init(&pfull[s], 1);
@@ -486,8 +487,10 @@ __global__ void __launch_bounds__(sv::TH, 1)
       }
     } else {
       // ------------------------------------------------------------ compute warps
-      const int kg = warp / L_CQ;           // k-group: slab kg of every block
-      const int cw = (warp % L_CQ) * L_CT;  // this warp's columns (of the leader's 16)
+      const int kg = warp / L_CQ;           // k-group: k in [kg L_KLEN, (kg + 1) L_KLEN)
+      const int cw = (warp % L_CQ) * L_CT;  // this warp's columns (of the leader's CG)
+      const int ks = kg * L_KLEN;
+      const int sl = ks >> 5, ch0 = (ks & 31) >> 2, ch1 = ch0 + L_KLEN / 4;
       long long gs = 0;
       for (int d = 0; d < nblk; ++d) {
         const int b = blk(d), buf = d & 1;
@@ -502,16 +505,16 @@ __global__ void __launch_bounds__(sv::TH, 1)
         for (int q = 0; q < m; ++q, gs += 4) {
           const float* V = q == 0 ? Ps + buf * CG * BS
                                   : Yr + ((d - (q == 1 && m == 3 ? 2 : 1)) % 3) * CG * BS;
-          const long long gk = gs + kg;  // this k-group's slab of the block
+          const long long gk = gs + sl;  // the slab of the block holding this k range
           const int slot = (int)(gk % LSLOTS);
           if (ok) ok = wait_bar(&sfull[slot], (uint32_t)(gk / LSLOTS) & 1, C, err, info, wait_ns);
-          // Li (lower): row groups kg..3 of slab kg; Li^T (upper): 0..kg
+          // Li (lower): row groups sl..3 of slab sl; Li^T (upper): 0..sl
           if (ok && q == 0)
-            slab_product<L_CT, true>(slabs + slot * SLAB_F, V, 32 * kg, 0, 8, cw, lane,
-                                     trans ? 0 : kg, trans ? kg : 3, acc);
+            slab_product<L_CT, true>(slabs + slot * SLAB_F, V, 32 * sl, ch0, ch1, cw, lane,
+                                     trans ? 0 : sl, trans ? sl : 3, acc);
           else if (ok)
-            slab_product<L_CT, false>(slabs + slot * SLAB_F, V, 32 * kg, 0, 8, cw, lane, 0, 3,
-                                      acc);
+            slab_product<L_CT, false>(slabs + slot * SLAB_F, V, 32 * sl, ch0, ch1, cw, lane, 0,
+                                      3, acc);
           __syncwarp();
           if (lane == 0) {
             tc::mbar_arrive(&sempty[slot]);

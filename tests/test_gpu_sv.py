@@ -60,7 +60,7 @@ def test_sv_potrs_is_deterministic(n, nrhs):
     B = inputs.uniform(n, nrhs, seed=12).to(torch.float32).to(DEV)
     first = None
     for _ in range(6):
-        Bd = B.t().contiguous().t()
+        Bd = jmg.colmajor_copy(B)  # a fresh copy: the solve works in place
         jmg.sv_potrs_(L, Bd)
         torch.cuda.synchronize()
         got = Bd.cpu()
