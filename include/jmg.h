@@ -65,7 +65,10 @@ enum {
 /* Options; pass NULL for the defaults of jmg_default_options(). */
 typedef struct {
   int nb;           /* diagonal-block / panel width (64 or 128)                     */
-  int NB;           /* depth of one trailing update (multiple of nb; 0 = nb)        */
+  int NB;           /* mixed modes: width of the outer blocks of the two-level      */
+                    /* factorisation, i.e. the depth (in columns of L) of one       */
+                    /* update of the trailing matrix (rounded down to a multiple of */
+                    /* nb, at least nb; 0 = nb)                                     */
   int prec;         /* jmg_prec                                                     */
   int words;        /* split words per tensor-core operand, 1..3 (BF16 / FP16)      */
   double tol;       /* target normwise backward error of posv (mixed modes)         */
@@ -105,7 +108,7 @@ typedef struct {
   long long d2h_bytes;    /* jmg_posv_host: bytes copied device -> host (0 otherwise)    */
 } jmg_stats;
 
-/* Fill *opt with the defaults: nb 128, NB 128, prec NATIVE, words 1, tol 1e-13,
+/* Fill *opt with the defaults: nb 128, NB 1024, prec NATIVE, words 1, tol 1e-13,
  * maxit 300, refine AUTO, shift_retry 1, timing 0, reuse_factor 0, resid 0. */
 void jmg_default_options(jmg_options* opt);
 

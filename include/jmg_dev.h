@@ -40,6 +40,17 @@ int jmg_dev_syrk_fp8(int m, int ncols, int kext, const void* Q, int ldq, const s
                      float* C, int ldc, int* err, void* stream);
 
 /*
+ * The same with one set of exponents per 128-deep chunk of K (the two-level
+ * factorisation applies several panels, each quantised with its own tile
+ * scales, in one update):
+ *     C[i, j] -= sum_c 2^-(e[c*lde + i/128] + e[c*lde + j/128]) * sum_{k in chunk c} Q[i, k] Q[j, k]
+ * lde >= ceil(m/128) (0: every chunk uses e[0 .. ceil(m/128)); kext % 128 == 0.
+ */
+int jmg_dev_syrk_fp8_chunks(int m, int ncols, int kext, const void* Q, int ldq,
+                            const signed char* e, int lde, float* C, int ldc, int* err,
+                            void* stream);
+
+/*
  * FP64 residual R = B - A X with A symmetric (lower(A) read), the kernel that
  * drives the refinement loop of jmg_posv.  X, B, R: n x nrhs column-major.
  * Also writes colmax[0..nrhs) = ||r_j||_inf, colmax[nrhs..2nrhs) = ||x_j||_inf,

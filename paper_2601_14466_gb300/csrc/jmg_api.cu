@@ -28,7 +28,7 @@ struct Plan {
          off_P = 0, off_Q = 0, off_scal = 0, off_sync = 0, off_exp = 0, off_ozrow = 0,
          off_ozA = 0, off_ozX = 0, off_SV = 0, total = 0;
   bool split = false;
-  int ldw = 0, ldp = 0, kext = 0, splits = 1, ldd = 0;
+  int ldw = 0, ldp = 0, kext = 0, splits = 1, ldd = 0, NB = 0, lde = 0;
 };
 
 static void opts_or_default(const jmg_options* in, jmg_options* out) {
@@ -55,8 +55,11 @@ static Plan plan_posv_mixed(int n, int nrhs, const jmg_options& o) {
   const size_t N = (size_t)n, R = (size_t)(nrhs > 0 ? nrhs : 1);
   p.ldw = (int)round_up(N > 0 ? N : 1, 32);
   p.ldd = p.ldw;  // the FP32 right-hand sides of the preconditioner solves
-  p.kext = o.prec == JMG_PREC_FP8 ? o.nb : o.nb * split_pairs(o.words);
-  p.ldp = (int)round_up((size_t)p.kext, 64);
+  p.kext = o.prec == JMG_PREC_FP8 ? o.nb : o.nb * split_pairs(o.words);  // one panel
+  // outer block width: a multiple of the panel width, at most n rounded up
+  p.NB = std::max(o.nb, std::min(o.NB / o.nb, cdiv(std::max(n, 1), o.nb)) * o.nb);
+  p.ldp = (int)round_up((size_t)p.kext * (p.NB / o.nb), o.prec == JMG_PREC_FP8 ? 128 : 64);
+  p.lde = n / 128 + 2;  // FP8 exponents per panel
   p.splits = residual_splits(n, nrhs > 0 ? nrhs : 1);
   // the factor and what a refine-only call (reuse_factor) needs come first, at
   // offsets that do not depend on nrhs
@@ -70,7 +73,7 @@ static Plan plan_posv_mixed(int n, int nrhs, const jmg_options& o) {
     p.off_ozA = take(oz_a_bytes(n));
   }
   p.off_PA = take(2 * N * p.ldp);  // 16-bit words, or e4m3 bytes for FP8
-  p.off_exp = take(N / 128 + 2);
+  p.off_exp = take((size_t)p.lde * (p.NB / o.nb));
   p.off_PB = take(2 * N * p.ldp);
   p.off_X = take(sizeof(double) * N * R);
   p.off_R = take(sizeof(double) * N * R);
@@ -126,21 +129,31 @@ static int potrf_plain(int n, T* A, int lda, int nb, int* info, cudaStream_t s) 
 
 // ---------------------------------------------------------------- mixed factor
 // Factor the FP32 working matrix W (lower) in place; info_f and err are device
-// ints of the workspace.  Right-looking over 128-wide panels.  The update of
-// step k is split in two: the next panel's columns first, then the rest of the
-// trailing matrix on one SM fewer; the next diagonal block (one CTA, bound by
-// its serial chain) is factored on a second stream on the free SM while the
-// rest of the update runs.  The panel solve and the word split of step k+1
-// follow both on the caller's stream.
+// ints of the workspace.  Two-level right-looking blocking:
+//  * outer blocks of NB columns (a multiple of the panel width nb);
+//  * inside a block, panel by panel: the panel solve below the diagonal block,
+//    the panel's split words (or FP8 codes) into column slot p of the block's
+//    operand, and the update of the block's remaining columns only (a narrow
+//    trapezoid, depth one panel);
+//  * after the block's last panel, ONE update of the whole trailing matrix with
+//    the block's operand (depth NB words per pair): the read-modify-write of the
+//    trailing matrix happens once per NB columns instead of once per panel.
+// Every update is split in two: the next panel's columns first, then the rest
+// on one SM fewer, while the next diagonal block (one CTA, bound by its serial
+// chain) is factored on a second stream on the free SM.
 static int factor_mixed(int n, float* W, int ldw, const jmg_options& o, const Plan& p,
                         void* work, int* info_f, int* err, cudaStream_t s) {
-  const int nb = o.nb;
-  void* PA = at<void>(work, p.off_PA);
-  void* PB = split_pairs(o.words) > 1 ? at<void>(work, p.off_PB) : PA;
+  const int nb = o.nb, NB = p.NB;
   const bool fp8 = o.prec == JMG_PREC_FP8;
+  const int kp = fp8 ? nb : nb * split_pairs(o.words);  // operand columns of one panel
+  char* PA = at<char>(work, p.off_PA);
+  char* PB = split_pairs(o.words) > 1 ? at<char>(work, p.off_PB) : PA;
   signed char* ex = fp8 ? at<signed char>(work, p.off_exp) : nullptr;
-  const int kext = fp8 ? nb : nb * split_pairs(o.words);
+  const int lde = p.lde;           // exponents: ex[panel * lde + 128-row tile of the operand]
   const size_t esz = fp8 ? 1 : 2;  // bytes per operand element
+  // operand row r of the current block <-> row k0 + r of W
+  auto opA = [&](size_t row, int col) { return PA + (row * p.ldp + col) * esz; };
+  auto opB = [&](size_t row, int col) { return PB + (row * p.ldp + col) * esz; };
   // the side stream and its events live for this call only
   struct Side {
     cudaStream_t s2 = nullptr;
@@ -160,45 +173,57 @@ static int factor_mixed(int n, float* W, int ldw, const jmg_options& o, const Pl
   JMG_CUDA(cudaGetDevice(&dev));
   JMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
 
-  JMG_TRY(launch_potf2(W, ldw, std::min(nb, n), 0, info_f, s));
-  for (int k = 0; k < n; k += nb) {
-    const int kb = std::min(nb, n - k);
-    float* Wkk = W + (size_t)k * ldw + k;
-    const int m = n - k - kb;
-    if (m <= 0) break;
-    float* L21 = Wkk + kb;
-    JMG_TRY(launch_trsm(L21, ldw, m, kb, Wkk, info_f, s));
-    float* W22 = W + (size_t)(k + kb) * ldw + (k + kb);
+  // C (rows x cols trapezoid at W[r0, r0]) -= operand rows [orow, orow + rows) x K columns
+  // [kc, kc + kext); FP8 exponents from panel kc / nb on (one chunk per panel)
+  auto update = [&](int r0, int rows, int cols, size_t orow, int kc, int kext, int ctas) -> int {
+    float* Cp = W + (size_t)r0 * ldw + r0;
     if (fp8)
-      JMG_TRY(launch_quant_fp8(m, kb, L21, ldw, PA, p.ldp, ex, s));
-    else
-      JMG_TRY(launch_split_words(m, kb, L21, ldw, o.prec, o.words, PA, PB, p.ldp, s));
-    // (P) the next panel's columns (all m rows, the diagonal tile masked)
-    const int pc = std::min(nb, m);
-    if (fp8)
-      JMG_TRY(launch_syrk_fp8(m, pc, kext, PA, p.ldp, ex, W22, ldw, err, s));
-    else
-      JMG_TRY(launch_syrk_tc(m, pc, kext, PA, PB, p.ldp, o.prec, W22, ldw, err, s));
-    // the next diagonal block, beside the rest of the update
+      return launch_syrk_fp8(rows, cols, kext, opA(orow, kc), p.ldp,
+                             ex + (size_t)(kc / nb) * lde + orow / 128, lde, Cp, ldw, err, s, ctas);
+    return launch_syrk_tc(rows, cols, kext, opA(orow, kc), opB(orow, kc), p.ldp, o.prec, Cp, ldw,
+                          err, s, ctas, 0, kp);
+  };
+  // the update of a trapezoid whose first nb columns hold the next diagonal
+  // block: those columns first, the block on the side stream, then the rest
+  auto update_lookahead = [&](int r0, int rows, int cols, size_t orow, int kc, int kext) -> int {
+    const int pc = std::min(nb, cols);
+    JMG_TRY(update(r0, rows, pc, orow, kc, kext, 0));
     JMG_CUDA(cudaEventRecord(side.panel, s));
     JMG_CUDA(cudaStreamWaitEvent(side.s2, side.panel, 0));
-    JMG_TRY(launch_potf2(W22, ldw, pc, k + kb, info_f, side.s2));
+    JMG_TRY(launch_potf2(W + (size_t)r0 * ldw + r0, ldw, std::min(nb, rows), r0, info_f, side.s2));
     JMG_CUDA(cudaEventRecord(side.diag, side.s2));
-    // (R) the trailing matrix right of the next panel, leaving one SM free
-    const int mr = m - pc;
-    if (mr > 0) {
-      float* W33 = W22 + (size_t)pc * ldw + pc;
-      const size_t off = (size_t)pc * p.ldp * esz;  // operand rows pc ..
-      const void* PAr = static_cast<const char*>(PA) + off;
-      const void* PBr = static_cast<const char*>(PB) + off;
-      if (fp8)
-        JMG_TRY(launch_syrk_fp8(mr, mr, kext, PAr, p.ldp, ex + pc / 128, W33, ldw, err, s,
-                                nsm - 1));
-      else
-        JMG_TRY(launch_syrk_tc(mr, mr, kext, PAr, PBr, p.ldp, o.prec, W33, ldw, err, s,
-                               nsm - 1));
-    }
+    if (cols > pc && rows > pc)
+      JMG_TRY(update(r0 + pc, rows - pc, cols - pc, orow + pc, kc, kext, nsm - 1));
     JMG_CUDA(cudaStreamWaitEvent(s, side.diag, 0));
+    return JMG_OK;
+  };
+
+  JMG_TRY(launch_potf2(W, ldw, std::min(nb, n), 0, info_f, s));
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int NBk = std::min(NB, n - k0);
+    const int q = cdiv(NBk, nb);
+    for (int pp = 0; pp < q; ++pp) {
+      const int k = k0 + pp * nb, kb = std::min(nb, n - k), m = n - k - kb;
+      if (m <= 0) break;
+      float* Wkk = W + (size_t)k * ldw + k;
+      float* L21 = Wkk + kb;
+      JMG_TRY(launch_trsm(L21, ldw, m, kb, Wkk, info_f, s));
+      const size_t orow = (size_t)(k + kb - k0);  // operand row of L21's first row
+      if (fp8)
+        JMG_TRY(launch_quant_fp8(m, kb, L21, ldw, opA(orow, pp * kp), p.ldp,
+                                 ex + (size_t)pp * lde + orow / 128, s));
+      else
+        JMG_TRY(launch_split_words(m, kb, L21, ldw, o.prec, o.words, opA(orow, pp * kp),
+                                   opB(orow, pp * kp), p.ldp, s));
+      const int ncb = k0 + NBk - (k + kb);  // columns of this block right of the panel
+      if (ncb > 0) {
+        // the block's remaining columns, with this panel's words only
+        JMG_TRY(update_lookahead(k + kb, m, ncb, orow, pp * kp, kp));
+      } else {
+        // the block is factored: the whole trailing matrix, with every panel of it
+        JMG_TRY(update_lookahead(k + kb, m, m, orow, 0, q * kp));
+      }
+    }
   }
   // the solves' images: inverses of the diagonal blocks, coupling blocks, and
   // L mirrored into the upper triangle of W
@@ -636,7 +661,7 @@ extern "C" {
 void jmg_default_options(jmg_options* o) {
   if (!o) return;
   o->nb = 128;
-  o->NB = 128;
+  o->NB = 1024;
   o->prec = JMG_PREC_NATIVE;
   o->words = 1;
   o->tol = 1e-13;
@@ -888,7 +913,18 @@ int jmg_dev_syrk_fp8(int m, int ncols, int kext, const void* Q, int ldq, const s
   if (ncols < 0 || ncols > m) return -2;
   if (ldc < std::max(1, m)) return -8;
   if (!err) return -9;
-  return launch_syrk_fp8(m, ncols, kext, Q, ldq, e, C, ldc, err, (cudaStream_t)stream);
+  return launch_syrk_fp8(m, ncols, kext, Q, ldq, e, 0, C, ldc, err, (cudaStream_t)stream);
+}
+
+int jmg_dev_syrk_fp8_chunks(int m, int ncols, int kext, const void* Q, int ldq,
+                            const signed char* e, int lde, float* C, int ldc, int* err,
+                            void* stream) {
+  if (m < 0) return -1;
+  if (ncols < 0 || ncols > m) return -2;
+  if (lde < 0) return -7;
+  if (ldc < std::max(1, m)) return -9;
+  if (!err) return -10;
+  return launch_syrk_fp8(m, ncols, kext, Q, ldq, e, lde, C, ldc, err, (cudaStream_t)stream);
 }
 
 size_t jmg_dev_residual_workspace(int n, int nrhs) {

@@ -18,6 +18,9 @@
 //                       epilogue of this one;
 //   warps 2-9:         epilogue     -- tcgen05.ld 32 lanes x 32 columns, then
 //                       C -= acc with coalesced column accesses (lane = row);
+//                       with FP8 every 128-deep chunk of K carries its own
+//                       power-of-two tile scales, so the chunks accumulate in
+//                       TMEM one at a time and the epilogue adds them scaled;
 //                       two warps per TMEM lane quarter, 64 columns each.  They
 //                       prefetch the next tile's C into L2 before they drain
 //                       this one, so the read-modify-write of C meets L2.
@@ -76,8 +79,8 @@ template <int KIND>
 __global__ void __launch_bounds__(PTHREADS, 1)
     k_syrk_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               float* __restrict__ C, int ldc, int m, int ncols, int kext, int ab_fmt,
-              int ntiles, int TJ, const signed char* __restrict__ exps, int* __restrict__ err,
-              unsigned long long wait_ns, int hold_producer) {
+              int ntiles, int TJ, const signed char* __restrict__ exps, int lde, int cstages,
+              int* __restrict__ err, unsigned long long wait_ns, int hold_producer) {
   extern __shared__ __align__(1024) unsigned char sm_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(sm_raw) + 1023) & ~uintptr_t(1023));
@@ -142,45 +145,51 @@ __global__ void __launch_bounds__(PTHREADS, 1)
       }
     }
   } else if (warp == 1) {
+    // MMA issuer: every chunk of `cstages` stages goes to an accumulator of its
+    // own (two, alternating), so the epilogue adds the chunks in registers with
+    // FP32 rounding (a long K summed inside one accumulator loses accuracy) and,
+    // for FP8, applies each chunk's own tile scales
     if (lane == 0) {
       const uint32_t idesc = idesc_f16(BM, BN, ab_fmt);
-      long long g = 0;
-      int i = 0;
-      for (int b = blockIdx.x; b < ntiles; b += gridDim.x, ++i) {
-        const int a = i & 1;
-        if (i >= 2 && !mbar_wait(&acc_empty[a], (uint32_t)((i / 2) - 1) & 1, wait_ns)) {
-          atomicExch(&s_fail, 1);
-          break;
-        }
-        tc_fence_after();
-        const uint32_t dacc = tmem + (uint32_t)(a * BN);
-        bool ok = true;
-        for (int kb = 0; kb < nk; ++kb, ++g) {
-          const int s = (int)(g % PSTAGES);
-          if (!mbar_wait(&full[s], (uint32_t)(g / PSTAGES) & 1, wait_ns)) {
+      const int nch = nk / cstages;
+      long long g = 0, ci = 0;
+      bool ok = true;
+      for (int b = blockIdx.x; b < ntiles && ok; b += gridDim.x) {
+        for (int c = 0; c < nch && ok; ++c, ++ci) {
+          const int a = (int)(ci & 1);
+          if (ci >= 2 && !mbar_wait(&acc_empty[a], (uint32_t)((ci / 2) - 1) & 1, wait_ns)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-          const uint32_t sb = sa + TILE_BYTES;
+          const uint32_t dacc = tmem + (uint32_t)(a * BN);
+          for (int kb = 0; kb < cstages; ++kb, ++g) {
+            const int s = (int)(g % PSTAGES);
+            if (!mbar_wait(&full[s], (uint32_t)(g / PSTAGES) & 1, wait_ns)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+            const uint32_t sb = sa + TILE_BYTES;
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {  // 4 x 32 bytes of K per stage
-            if (KIND == 0)
-              tc_mma_f16(dacc, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
-                         (kb > 0 || kk > 0) ? 1u : 0u);
-            else
-              tc_mma_f8(dacc, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
-                        (kb > 0 || kk > 0) ? 1u : 0u);
+            for (int kk = 0; kk < 4; ++kk) {  // 4 x 32 bytes of K per stage
+              if (KIND == 0)
+                tc_mma_f16(dacc, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
+                           (kb > 0 || kk > 0) ? 1u : 0u);
+              else
+                tc_mma_f8(dacc, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
+                          (kb > 0 || kk > 0) ? 1u : 0u);
+            }
+            tc_commit(&empty[s]);
           }
-          tc_commit(&empty[s]);
-        }
-        tc_commit(&acc_full[a]);
-        if (!ok) {
-          atomicExch(&s_fail, 1);
-          break;
+          // on failure the flag goes first, so that the epilogue, released by the
+          // arrival below, leaves C alone
+          if (!ok) atomicExch(&s_fail, 1);
+          tc_commit(&acc_full[a]);
         }
       }
+      if (!ok) atomicExch(&s_fail, 1);
     }
   } else {
     // epilogue warps 2..9
@@ -201,43 +210,67 @@ __global__ void __launch_bounds__(PTHREADS, 1)
       }
     };
     prefetch_c(blockIdx.x);
-    int i = 0;
-    for (int b = blockIdx.x; b < ntiles; b += gridDim.x, ++i) {
+    // the chunks of a tile add up in registers (this warp's 32 rows x 64
+    // columns), then one read-modify-write of C per tile
+    const int nch = nk / cstages;
+    long long ci = 0;
+    bool ok = true;
+    for (int b = blockIdx.x; b < ntiles && ok; b += gridDim.x) {
       int ti, tj;
       trap_index(b, TJ, ti, tj);
       prefetch_c(b + gridDim.x);
-      const int a = i & 1;
-      const bool ok = mbar_wait(&acc_full[a], (uint32_t)(i / 2) & 1, wait_ns);
-      tc_fence_after();
-      if (!ok || ld_shared_volatile(&s_fail)) {
+      float acc[2][32];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[h][j] = 0.0f;
+      for (int c = 0; c < nch; ++c, ++ci) {
+        const int a = (int)(ci & 1);
+        ok = mbar_wait(&acc_full[a], (uint32_t)(ci / 2) & 1, wait_ns);
+        tc_fence_after();
+        if (!ok || ld_shared_volatile(&s_fail)) {
+          ok = false;
+          break;
+        }
+        float scale = 1.0f;
+        if (KIND == 1) {
+          const signed char* ek = exps + (size_t)c * lde;
+          scale = exp2f(-(float)((int)ek[ti] + (int)ek[tj]));
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN + ch + 32 * h), v);
+          tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc[h][j] = fmaf(scale, __uint_as_float(v[j]), acc[h][j]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[a]);
+      }
+      if (!ok) {
         atomicExch(&s_fail, 1);
         break;
       }
       const int r = ti * BM + q * 32 + lane;
       const bool diag = (ti == tj);
-      const float scale = (KIND == 1) ? exp2f(-(float)((int)exps[ti] + (int)exps[tj])) : 1.0f;
-#pragma unroll 1
-      for (int c0 = ch; c0 < ch + BN / 2; c0 += 32) {
-        uint32_t v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN + c0), v);
-        tmem_ld_wait();
-        if (r < m) {
-          // all 32 loads first (independent, coalesced across the warp), then the stores
-          const int cb = tj * BN + c0;
+      if (r < m) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int cb = tj * BN + ch + 32 * h;
           float* cp = C + (size_t)cb * ldc + r;
           // columns j < jn of this chunk are in range (and on or below the diagonal)
           const int jn = min(32, min(ncols - cb, diag ? r - cb + 1 : 32));
+          // all 32 loads first (independent, coalesced across the warp), then the stores
           float old[32];
 #pragma unroll
           for (int j = 0; j < 32; ++j) old[j] = j < jn ? cp[j * ldc] : 0.0f;
 #pragma unroll
           for (int j = 0; j < 32; ++j)
-            if (j < jn) cp[j * ldc] = old[j] - scale * __uint_as_float(v[j]);
+            if (j < jn) cp[j * ldc] = old[j] - acc[h][j];
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[a]);
     }
   }
   __syncwarp();
@@ -311,9 +344,14 @@ static int make_map(CUtensorMap* map, const void* base, int rows, int cols, int 
 }
 
 template <int KIND>
-static int syrk_persistent(int m, int ncols, int kext, const CUtensorMap& ma, const CUtensorMap& mb,
-                           int ab_fmt, const signed char* exps, float* C, int ldc, int* err,
-                           cudaStream_t s, int max_ctas, int hold = 0) {
+static int syrk_persistent(int m, int ncols, int kext, int kchunk, const CUtensorMap& ma,
+                           const CUtensorMap& mb, int ab_fmt, const signed char* exps, int lde,
+                           float* C, int ldc, int* err, cudaStream_t s, int max_ctas,
+                           int hold = 0) {
+  const int stage_k = KIND == 0 ? tc::BK : 2 * tc::BK;  // K elements per stage
+  if (kchunk <= 0 || kchunk > kext) kchunk = kext;
+  if (kchunk % stage_k || kext % kchunk) return JMG_ERR_ALIGN;
+  const int cstages = kchunk / stage_k;
   int dev = 0, nsm = 0;
   JMG_CUDA(cudaGetDevice(&dev));
   JMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -322,12 +360,14 @@ static int syrk_persistent(int m, int ncols, int kext, const CUtensorMap& ma, co
   const long long ntiles = (long long)TJ * (TJ + 1) / 2 + (long long)(TI - TJ) * TJ;
   const int grid = (int)std::min<long long>(ntiles, max_ctas > 0 ? std::min(max_ctas, nsm) : nsm);
   tc::k_syrk_tc<KIND><<<grid, tc::PTHREADS, tc::PSMEM_BYTES, s>>>(
-      ma, mb, C, ldc, m, ncols, kext, ab_fmt, (int)ntiles, TJ, exps, err, g_wait_ns, hold);
+      ma, mb, C, ldc, m, ncols, kext, ab_fmt, (int)ntiles, TJ, exps, lde, cstages, err, g_wait_ns,
+      hold);
   return launched();
 }
 
 int launch_syrk_tc(int m, int ncols, int kext, const void* PA, const void* PB, int ldp, int prec,
-                   float* C, int ldc, int* err, cudaStream_t s, int max_ctas, int hold) {
+                   float* C, int ldc, int* err, cudaStream_t s, int max_ctas, int hold,
+                   int kchunk) {
   if (m <= 0 || ncols <= 0 || kext <= 0) return JMG_OK;
   if (ncols > m) return JMG_ERR_UNSUPPORTED;
   if (kext % tc::BK || ldp % 64 || ldp < kext) return JMG_ERR_ALIGN;
@@ -338,12 +378,12 @@ int launch_syrk_tc(int m, int ncols, int kext, const void* PA, const void* PB, i
   CUtensorMap ma, mb;
   JMG_TRY(make_map(&ma, PA, m, kext, ldp, 2, dt));
   JMG_TRY(make_map(&mb, PB, m, kext, ldp, 2, dt));
-  return syrk_persistent<0>(m, ncols, kext, ma, mb, prec == JMG_PREC_BF16 ? 1 : 0, nullptr, C, ldc,
-                            err, s, max_ctas, hold);
+  return syrk_persistent<0>(m, ncols, kext, kchunk, ma, mb, prec == JMG_PREC_BF16 ? 1 : 0, nullptr,
+                            0, C, ldc, err, s, max_ctas, hold);
 }
 
 int launch_syrk_fp8(int m, int ncols, int kext, const void* Q, int ldq, const signed char* e,
-                    float* C, int ldc, int* err, cudaStream_t s, int max_ctas) {
+                    int lde, float* C, int ldc, int* err, cudaStream_t s, int max_ctas) {
   if (m <= 0 || ncols <= 0 || kext <= 0) return JMG_OK;
   if (ncols > m) return JMG_ERR_UNSUPPORTED;
   if (kext % 128 || ldq % 128 || ldq < kext) return JMG_ERR_ALIGN;
@@ -351,7 +391,7 @@ int launch_syrk_fp8(int m, int ncols, int kext, const void* Q, int ldq, const si
   if (!e) return JMG_ERR_UNSUPPORTED;
   CUtensorMap mq;
   JMG_TRY(make_map(&mq, Q, m, kext, ldq, 1, CU_TENSOR_MAP_DATA_TYPE_UINT8));
-  return syrk_persistent<1>(m, ncols, kext, mq, mq, 0, e, C, ldc, err, s, max_ctas);
+  return syrk_persistent<1>(m, ncols, kext, 128, mq, mq, 0, e, lde, C, ldc, err, s, max_ctas);
 }
 
 }  // namespace jmg

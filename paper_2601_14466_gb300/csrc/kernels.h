@@ -175,11 +175,17 @@ int make_tmap_2d(CUtensorMap* map, const void* base, unsigned long long inner,
 // max_ctas > 0 caps the persistent grid (to leave SMs free for concurrent work).
 // hold != 0 is a test hook: the TMA producer stays idle, so the kernel's first
 // bounded wait runs out (g_wait_ns) and it returns through its abort path.
+// kchunk (a multiple of 64 dividing kext; 0 = kext): K goes to the tensor-core
+// accumulator in chunks of kchunk and the chunks add up in FP32 registers.
 int launch_syrk_tc(int m, int ncols, int kext, const void* PA, const void* PB, int ldp, int prec,
-                   float* C, int ldc, int* err, cudaStream_t s, int max_ctas = 0, int hold = 0);
-// FP8 e4m3 variant: Q (m x kext bytes, row-major, ldq), C -= 2^-(e[ti]+e[tj]) Q_ti Q_tj^T
+                   float* C, int ldc, int* err, cudaStream_t s, int max_ctas = 0, int hold = 0,
+                   int kchunk = 0);
+// FP8 e4m3 variant: Q (m x kext bytes, row-major, ldq); K goes in chunks of 128,
+// chunk c with its own exponents e + c * lde (one per 128-row tile; lde = 0: the
+// same exponents for every chunk):
+//     C -= sum_c 2^-(e_c[ti] + e_c[tj]) Q_ti,c Q_tj,c^T
 int launch_syrk_fp8(int m, int ncols, int kext, const void* Q, int ldq, const signed char* e,
-                    float* C, int ldc, int* err, cudaStream_t s, int max_ctas = 0);
+                    int lde, float* C, int ldc, int* err, cudaStream_t s, int max_ctas = 0);
 // Quantise the FP32 panel L21 (m x kb, ldw) to e4m3 with one power-of-two scale
 // per 128-row tile: e = floor(log2(448 / amax)) clamped to [-126, 126] (0 for an
 // all-zero tile), Q = rn_satfinite(x * 2^e), row-major m x kb (ldq bytes).

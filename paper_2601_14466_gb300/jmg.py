@@ -85,6 +85,7 @@ _SIGS = {
     "jmg_sym_grad": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P]),
     "jmg_dev_syrk_tc": (_I, [_I, _I, _I, _P, _P, _I, _I, _P, _I, _P, _P]),
     "jmg_dev_syrk_fp8": (_I, [_I, _I, _I, _P, _I, _P, _P, _I, _P, _P]),
+    "jmg_dev_syrk_fp8_chunks": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _P]),
     "jmg_dev_residual_workspace": (_SZ, [_I, _I]),
     "jmg_dev_residual": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P, _SZ, _P]),
     "jmg_dev_residual_split_workspace": (_SZ, [_I, _I]),
@@ -508,6 +509,22 @@ def syrk_fp8_(C: torch.Tensor, Q: torch.Tensor, e: torch.Tensor,
     st = load().jmg_dev_syrk_fp8(m, m if ncols is None else ncols, kext, Q.data_ptr(), kext,
                                  e.data_ptr(), pc, ldc, err.data_ptr(), _stream(C.device))
     _chk(st, "jmg_dev_syrk_fp8")
+    return err
+
+
+def syrk_fp8_chunks_(C: torch.Tensor, Q: torch.Tensor, e: torch.Tensor) -> torch.Tensor:
+    """C_lower -= sum_c 2^-(e[c, i] + e[c, j]) Q_i,c Q_j,c^T over 128-deep chunks c of
+    K (Q: m x kext e4m3 bytes, e: (kext/128, lde) int8 exponents per chunk and
+    128-row tile; C: FP32 column-major)."""
+    _need_cuda(C, Q, e)
+    m, kext = Q.shape
+    if e.dim() != 2 or e.dtype != torch.int8 or not e.is_contiguous():
+        raise TypeError("syrk_fp8_chunks_: e must be a contiguous 2-D int8 tensor")
+    pc, ldc = _colmajor(C, "C")
+    err = torch.zeros(1, dtype=torch.int32, device=C.device)
+    st = load().jmg_dev_syrk_fp8_chunks(m, m, kext, Q.data_ptr(), kext, e.data_ptr(), e.shape[1],
+                                        pc, ldc, err.data_ptr(), _stream(C.device))
+    _chk(st, "jmg_dev_syrk_fp8_chunks")
     return err
 
 

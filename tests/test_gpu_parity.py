@@ -215,6 +215,34 @@ def test_syrk_fp8_exact_integers(m, ncols, kext):
     assert np.array_equal(got[~touched], C0.numpy()[~touched])
 
 
+@pytest.mark.parametrize("m,kext", [(300, 256), (1000, 512), (2600, 1024)])
+def test_syrk_fp8_chunk_scales_exact(m, kext):
+    # every 128-deep chunk of K has its own power-of-two tile exponents (one
+    # panel of the two-level factorisation each); with small integer codes and
+    # exponents in [-1, 1] every scaled partial sum needs at most 21 bits, so
+    # the FP32 accumulation is exact and the update must be bit-exact
+    g = torch.Generator().manual_seed(m * 7 + kext)
+    Qv = torch.randint(-8, 9, (m, kext), generator=g).to(torch.float64)
+    ntile, nch = (m + 127) // 128, kext // 128
+    e = torch.randint(-1, 2, (nch, ntile + 1), generator=g, dtype=torch.int8)
+    C0 = torch.randint(-1000, 1000, (m, m), generator=g).to(torch.float64)
+    want = C0.clone()
+    for c in range(nch):
+        rs = torch.pow(2.0, -e[c, :ntile].to(torch.float64)).repeat_interleave(128)[:m]
+        Qc = rs[:, None] * Qv[:, 128 * c:128 * (c + 1)]
+        want -= Qc @ Qc.t()
+    Q8 = Qv.to(torch.float32).to(torch.float8_e4m3fn).view(torch.uint8).contiguous().to(DEV)
+    Cd, _ = to_dev_colmajor(C0)
+    Cf = Cd.to(torch.float32).t().contiguous().t()
+    err = jmg.syrk_fp8_chunks_(Cf, Q8, e.contiguous().to(DEV))
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    got = Cf.double().cpu().numpy()
+    lo = np.tril(np.ones((m, m), dtype=bool))
+    assert np.array_equal(got[lo], want.numpy()[lo])
+    assert np.array_equal(got[~lo], C0.numpy()[~lo])
+
+
 def test_syrk_tc_exact_near_fp32_limit():
     # the split residual relies on exact FP32 accumulation of integer products
     # up to ~2^23 in TMEM: all-maximal slices (128 * 128 * 256 = 2^22) and random ones
