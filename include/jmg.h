@@ -44,7 +44,11 @@ typedef enum {
   JMG_PREC_NATIVE = 0, /* FP64 throughout (potrf / potrs in place)              */
   JMG_PREC_BF16 = 1,   /* BF16 tensor-core updates, FP32 accumulate, FP64 refine */
   JMG_PREC_FP16 = 2,   /* FP16 tensor-core updates, FP32 accumulate, FP64 refine */
-  JMG_PREC_FP8 = 3     /* FP8 e4m3, power-of-two scale per 128x128 tile          */
+  JMG_PREC_FP8 = 3,    /* FP8 e4m3, power-of-two scale per 128x128 tile          */
+  JMG_PREC_FP32 = 4    /* posv only, n <= 2048, nrhs <= 64: FP32 factor on CUDA
+                          cores and FP64 refinement in ONE persistent kernel
+                          (the stopping rule runs on the device; classic IR,
+                          no PCG switch); larger problems: JMG_ERR_UNSUPPORTED */
 } jmg_prec;
 
 typedef enum { JMG_REFINE_IR = 0, JMG_REFINE_PCG = 1, JMG_REFINE_AUTO = 2 } jmg_refine;
@@ -191,6 +195,12 @@ int jmg_potrs_static_status(int* status, void* stream);
  *     synchronises `stream` once per refinement iteration and returns only when
  *     X is final.  B is overwritten with X.  FP64 data only (JMG_F32 returns
  *     JMG_ERR_UNSUPPORTED).
+ *   prec == FP32 (n <= 2048, nrhs <= 64): the same solve as ONE persistent
+ *     cooperative kernel: FP32 tile Cholesky (shifted and refactored on the
+ *     device after a breakdown when opt->shift_retry), FP64 residuals and the
+ *     stopping rule on the device; the call synchronises `stream` once, after
+ *     the kernel, to read the status.  opt->nb, NB, words, refine and resid
+ *     are ignored.  Larger problems return JMG_ERR_UNSUPPORTED.
  *   info    device int (potrf convention); may not be NULL
  *   stats   host pointer or NULL
  */
@@ -267,6 +277,29 @@ int jmg_logdet(int n, const void* L, int lda, int dtype, double* out, void* stre
  */
 int jmg_sym_grad(int n, int nrhs, const double* Bbar, int ldb, const double* X, int ldx,
                  double* Abar, int ldab, void* stream);
+
+/*
+ * rowmajor_to_colmajor -- in-place layout conversion (paper: "Local
+ * memory-layout conversion": a row-major array of the framework becomes the
+ * column-major buffer the solver wants, without a second full-sized copy).
+ *   m, n    rows and columns of the matrix M (m, n >= 0)
+ *   A       device, m * n elements: on entry M row-major (M(i, j) at i n + j),
+ *           on exit M column-major (M(i, j) at i + j m, i.e. the buffer holds
+ *           the row-major n x m matrix M^T); the logical matrix is unchanged
+ *   dtype   JMG_F64 or JMG_F32 (the elements are moved bit for bit)
+ *   work    device scratch, at least jmg_layout_workspace(m, n, dtype) bytes;
+ *           a larger buffer lets more column batches run at once (the move is
+ *           done in batches bounded by it)
+ * colmajor_to_rowmajor is the inverse move (a column-major m x n M back to
+ * row-major), with scratch jmg_layout_workspace(n, m, dtype).
+ * Asynchronous.  Returns JMG_OK, -i for an illegal argument i, or
+ * JMG_ERR_WORKSPACE.
+ */
+size_t jmg_layout_workspace(long long m, long long n, int dtype);
+int jmg_rowmajor_to_colmajor(long long m, long long n, void* A, int dtype, void* work,
+                             size_t lwork, void* stream);
+int jmg_colmajor_to_rowmajor(long long m, long long n, void* A, int dtype, void* work,
+                             size_t lwork, void* stream);
 
 /* Human-readable name of a status code. */
 const char* jmg_status_string(int status);

@@ -76,6 +76,8 @@ class Oracle:
         lib.oracle_bwd_err.restype = ctypes.c_double
         lib.oracle_bwd_err_rows.argtypes = [_I, _I, _D, _I, _D, _I, _D, _I, _D]
         lib.oracle_bwd_err_rows.restype = ctypes.c_double
+        lib.oracle_rowmajor_to_colmajor.argtypes = [ctypes.c_longlong, ctypes.c_longlong, _D, _D]
+        lib.oracle_rowmajor_to_colmajor.restype = None
         lib.oracle_logdet.argtypes = [_I, _D, _I]
         lib.oracle_logdet.restype = ctypes.c_double
         lib.oracle_grad.argtypes = [_I, _I, _D, _I, _D, _I, _D, _I, _D, _D, _D, _I]
@@ -153,6 +155,15 @@ class Oracle:
         worst = self.lib.oracle_bwd_err_rows(n, nrhs, _p(A), _ld(A), _p(X), _ld(X), _p(B),
                                              _ld(B), _p(eta))
         return float(worst), eta
+
+    def rowmajor_to_colmajor(self, buf, m, n):
+        """The m*n buffer holding an m x n matrix row-major, rewritten in
+        column-major order (a new flat float64 array)."""
+        src = np.ascontiguousarray(np.asarray(buf, dtype=np.float64).reshape(-1))
+        assert src.size == m * n
+        out = np.empty(m * n)
+        self.lib.oracle_rowmajor_to_colmajor(m, n, _p(src), _p(out))
+        return out
 
     def logdet(self, L) -> float:
         """log det A = 2 sum log L_ii from a lower Cholesky factor."""
@@ -240,6 +251,10 @@ def bwd_err(A, X, B):
 
 def bwd_err_rows(A, X, B):
     return default().bwd_err_rows(A, X, B)
+
+
+def rowmajor_to_colmajor(buf, m, n):
+    return default().rowmajor_to_colmajor(buf, m, n)
 
 
 def logdet(L) -> float:

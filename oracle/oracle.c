@@ -30,6 +30,8 @@
  *   oracle_bwd_err_rows  the same numbers, bit for bit, with the loops arranged
  *                  so that a matrix of tens of GB is read once (certification
  *                  of full-size results).
+ *   oracle_rowmajor_to_colmajor  the layout conversion of the paper's
+ *                  "Local memory-layout conversion" stage, by its definition.
  *   oracle_logdet  log det A = 2 sum_i log L_ii (paper: "Software design",
  *                  potrs can also return log det A).
  *   oracle_grad    adjoint of X = A^{-1} B for symmetric A:
@@ -259,6 +261,15 @@ double oracle_bwd_err_rows(int n, int nrhs, const double* A, int lda, const doub
   free(r);
   free(rowsum);
   return worst;
+}
+
+/* Row-major to column-major order (paper: "Local memory-layout conversion"),
+ * out of place, by its definition: the m x n matrix held row-major in `in`
+ * (element (i, j) at i n + j) is written column-major to `out` (element (i, j)
+ * at i + j m). */
+void oracle_rowmajor_to_colmajor(long long m, long long n, const double* in, double* out) {
+  for (long long i = 0; i < m; ++i)
+    for (long long j = 0; j < n; ++j) out[i + j * m] = in[i * n + j];
 }
 
 double oracle_logdet(int n, const double* L, int lda) {

@@ -14,6 +14,7 @@
 //   untouched A) until the normwise backward error reaches `tol`.
 #include <chrono>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "../../include/jmg_dev.h"
@@ -102,6 +103,32 @@ static size_t plain_solve_bytes(int n, int nrhs) {
   return round_up(sizeof(int) * trsv_sync_ints(n, nrhs), 256);
 }
 
+// Side streams and events of the mixed path, created once per device on first
+// use and kept for the life of the process (a call made on another thread
+// shares them: events are re-recorded, which can only add dependencies).
+struct DevAux {
+  cudaStream_t hi = nullptr, lo = nullptr;  // high / low priority, non-blocking
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+static int dev_aux(DevAux** out) {
+  static std::mutex mu;
+  static DevAux aux[64];
+  int dev = 0;
+  JMG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return JMG_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(mu);
+  DevAux& a = aux[dev];
+  if (!a.hi) {
+    int prio_lo = 0, prio_hi = 0;
+    JMG_CUDA(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+    JMG_CUDA(cudaStreamCreateWithPriority(&a.lo, cudaStreamNonBlocking, prio_lo));
+    for (auto& e : a.ev) JMG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    JMG_CUDA(cudaStreamCreateWithPriority(&a.hi, cudaStreamNonBlocking, prio_hi));
+  }
+  *out = &a;
+  return JMG_OK;
+}
+
 template <typename T>
 static T* at(void* work, size_t off) {
   return reinterpret_cast<T*>(reinterpret_cast<char*>(work) + off);
@@ -154,21 +181,13 @@ static int factor_mixed(int n, float* W, int ldw, const jmg_options& o, const Pl
   // operand row r of the current block <-> row k0 + r of W
   auto opA = [&](size_t row, int col) { return PA + (row * p.ldp + col) * esz; };
   auto opB = [&](size_t row, int col) { return PB + (row * p.ldp + col) * esz; };
-  // the side stream and its events live for this call only
-  struct Side {
-    cudaStream_t s2 = nullptr;
-    cudaEvent_t panel = nullptr, diag = nullptr;
-    ~Side() {
-      if (panel) cudaEventDestroy(panel);
-      if (diag) cudaEventDestroy(diag);
-      if (s2) cudaStreamDestroy(s2);
-    }
-  } side;
-  int prio_lo = 0, prio_hi = 0;
-  JMG_CUDA(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
-  JMG_CUDA(cudaStreamCreateWithPriority(&side.s2, cudaStreamNonBlocking, prio_hi));
-  JMG_CUDA(cudaEventCreateWithFlags(&side.panel, cudaEventDisableTiming));
-  JMG_CUDA(cudaEventCreateWithFlags(&side.diag, cudaEventDisableTiming));
+  // the high-priority side stream and its events (made once per device)
+  DevAux* aux = nullptr;
+  JMG_TRY(dev_aux(&aux));
+  struct {
+    cudaStream_t s2;
+    cudaEvent_t panel, diag;
+  } side{aux->hi, aux->ev[0], aux->ev[1]};
   int dev = 0, nsm = 152;
   JMG_CUDA(cudaGetDevice(&dev));
   JMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -450,20 +469,15 @@ static int posv_mixed(int n, int nrhs, const double* A, int lda, double* B, int 
       pending = false;
       return JMG_OK;
     }
-    ~Prologue() {
-      (void)wait();
-      if (start) cudaEventDestroy(start);
-      if (done) cudaEventDestroy(done);
-      if (s3) cudaStreamDestroy(s3);
-    }
+    ~Prologue() { (void)wait(); }
   } pro;
   pro.main = s;
   if (!o.reuse_factor) {
-    int prio_lo = 0, prio_hi = 0;
-    JMG_CUDA(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
-    JMG_CUDA(cudaStreamCreateWithPriority(&pro.s3, cudaStreamNonBlocking, prio_lo));
-    JMG_CUDA(cudaEventCreateWithFlags(&pro.start, cudaEventDisableTiming));
-    JMG_CUDA(cudaEventCreateWithFlags(&pro.done, cudaEventDisableTiming));
+    DevAux* aux = nullptr;
+    JMG_TRY(dev_aux(&aux));
+    pro.s3 = aux->lo;  // the low-priority side stream and its events (made once per device)
+    pro.start = aux->ev[2];
+    pro.done = aux->ev[3];
     JMG_CUDA(cudaEventRecord(pro.start, s));  // A and the workspace are ready here
     JMG_CUDA(cudaStreamWaitEvent(pro.s3, pro.start, 0));
     if (p.split) {  // one pass for the row sums (||A||_inf) and row maxima (slice scales)
@@ -681,6 +695,8 @@ size_t jmg_workspace_size(int op, int n, int nrhs, int dtype, const jmg_options*
     const size_t es = dtype == JMG_F32 ? sizeof(float) : sizeof(double);
     return host_stage(n, nrhs, es).off_posv + jmg_workspace_size(JMG_OP_POSV, n, nrhs, dtype, &o);
   }
+  if (op == JMG_OP_POSV && o.prec == JMG_PREC_FP32)
+    return small_path_fits(n, nrhs) ? small_workspace(n, nrhs) : 0;
   if (op == JMG_OP_POSV && o.prec != JMG_PREC_NATIVE && n > 0)
     return plan_posv_mixed(n, nrhs, o).total;
   if (op == JMG_OP_POSV || op == JMG_OP_POTRS) return plain_solve_bytes(n, nrhs);
@@ -774,6 +790,16 @@ int jmg_posv(int n, int nrhs, void* A, int lda, void* B, int ldb, int dtype, int
     return JMG_OK;
   }
   if (dtype == JMG_F32) return JMG_ERR_UNSUPPORTED;  // mixed modes refine FP64 data
+  if (o.prec == JMG_PREC_FP32) {
+    if (!small_path_fits(n, nrhs)) return JMG_ERR_UNSUPPORTED;
+    if (nrhs == 0) {
+      JMG_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
+      return JMG_OK;
+    }
+    if (!work || lwork < small_workspace(n, nrhs)) return JMG_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(work) & 255) return JMG_ERR_ALIGN;
+    return small_posv(n, nrhs, (const double*)A, lda, (double*)B, ldb, info, o, stats, work, s);
+  }
   if (o.prec != JMG_PREC_BF16 && o.prec != JMG_PREC_FP16 && o.prec != JMG_PREC_FP8)
     return JMG_ERR_UNSUPPORTED;
   if (o.prec == JMG_PREC_FP8 && o.nb != 128) return -9;
@@ -809,8 +835,9 @@ int jmg_posv_host(int n, int nrhs, const void* A, int lda, const void* B, int ld
   if (nrhs > 0 && !X) return -7;
   if (o.prec != JMG_PREC_NATIVE && dtype == JMG_F32) return JMG_ERR_UNSUPPORTED;
   if (o.prec != JMG_PREC_NATIVE && o.prec != JMG_PREC_BF16 && o.prec != JMG_PREC_FP16 &&
-      o.prec != JMG_PREC_FP8)
+      o.prec != JMG_PREC_FP8 && o.prec != JMG_PREC_FP32)
     return JMG_ERR_UNSUPPORTED;
+  if (o.prec == JMG_PREC_FP32 && !small_path_fits(n, nrhs)) return JMG_ERR_UNSUPPORTED;
   const size_t es = dtype == JMG_F32 ? sizeof(float) : sizeof(double);
   const HostStage h = host_stage(n, nrhs, es);
   const size_t need = jmg_workspace_size(JMG_OP_POSV_HOST, n, nrhs, dtype, &o);

@@ -163,6 +163,17 @@ inline int sv_solve_llt(int n, int nrhs, const float* W, int ldw, const float* S
   return sv_solve(n, nrhs, W, ldw, SV, D, ldd, 1, sync, info, s);
 }
 
+// ---- in-place row-major -> column-major conversion (k_layout.cu)
+size_t layout_min_scratch(long long m, long long n, size_t esize);
+
+// k_small.cu: the whole mixed posv for n <= 2048 in one persistent kernel
+bool small_path_fits(int n, int nrhs);
+size_t small_workspace(int n, int nrhs);
+int small_posv(int n, int nrhs, const double* A, int lda, double* B, int ldb, int* info,
+               const jmg_options& o, jmg_stats* st, void* work, cudaStream_t s);
+int layout_r2c(long long m, long long n, void* A, int dtype, void* work, size_t lwork,
+               cudaStream_t s);
+
 // 2D tiled tensor map over a matrix with `inner` contiguous elements per line
 // (leading dimension ld_bytes), `outer` lines; box box_inner x box_outer.
 int make_tmap_2d(CUtensorMap* map, const void* base, unsigned long long inner,

@@ -27,7 +27,7 @@ _lock = threading.Lock()
 _lib = None
 
 JMG_F64, JMG_F32 = 0, 1
-PREC = {"fp64": 0, "native": 0, "bf16": 1, "fp16": 2, "fp8": 3}
+PREC = {"fp64": 0, "native": 0, "bf16": 1, "fp16": 2, "fp8": 3, "fp32": 4}
 REFINE = {"ir": 0, "pcg": 1, "auto": 2}
 OP_POTRF, OP_POTRS, OP_POSV, OP_POSV_HOST = 0, 1, 2, 3
 
@@ -102,6 +102,9 @@ _SIGS = {
     "jmg_potrs_static_status": (_I, [ctypes.POINTER(_I), _P]),
     "jmg_posv_batched": (_I, [_I, _I, _I, _P, _I, ctypes.c_longlong, _P, _I, ctypes.c_longlong, _I,
                               _P, _P]),
+    "jmg_layout_workspace": (_SZ, [ctypes.c_longlong, ctypes.c_longlong, _I]),
+    "jmg_rowmajor_to_colmajor": (_I, [ctypes.c_longlong, ctypes.c_longlong, _P, _I, _P, _SZ, _P]),
+    "jmg_colmajor_to_rowmajor": (_I, [ctypes.c_longlong, ctypes.c_longlong, _P, _I, _P, _SZ, _P]),
 }
 
 
@@ -283,7 +286,9 @@ def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1
     prec "fp64": potrf + potrs in FP64 (A is overwritten with L only when
     ``overwrite_a``; otherwise a copy is factored).  prec "bf16"/"fp16": mixed
     precision with tensor-core trailing updates and FP64 refinement; A is
-    preserved.  Returns ``(X, SolveInfo)``; X is a new column-major tensor."""
+    preserved.  prec "fp32" (n <= 2048, nrhs <= 64): FP32 factor and FP64
+    refinement in one persistent kernel with the stopping rule on the device.
+    Returns ``(X, SolveInfo)``; X is a new column-major tensor."""
     _need_cuda(A, B)
     if A.dtype != B.dtype or A.dtype not in (torch.float64, torch.float32):
         raise TypeError("posv: A and B must both be float64 (any mode) or both float32 "
@@ -397,6 +402,43 @@ def posv_batched(A: torch.Tensor, B: torch.Tensor):
                                  max(n, 1), n * nrhs, dt, info.data_ptr(), _stream(A.device))
     _chk(st, "jmg_posv_batched")
     return Xw.transpose(1, 2), Lw, info[:batch]
+
+
+def to_colmajor_(t: torch.Tensor, work: torch.Tensor | None = None) -> torch.Tensor:
+    """Convert a contiguous row-major m x n CUDA tensor (float64 or float32) to
+    column-major order IN PLACE (no second full-sized buffer) and return the
+    column-major view of the same storage (same logical matrix, stride (1, m)).
+    ``work``: optional device byte tensor of at least
+    ``jmg_layout_workspace(m, n)`` bytes (more lets more column batches run at
+    once)."""
+    _need_cuda(t)
+    if t.dim() != 2 or not t.is_contiguous():
+        raise ValueError("to_colmajor_: a contiguous (row-major) 2-D tensor is required")
+    m, n = t.shape
+    dt = _dtype_code(t)
+    need = int(load().jmg_layout_workspace(m, n, dt))
+    if work is None:
+        work = torch.empty(max(need, 256), dtype=torch.uint8, device=t.device)
+    _chk(load().jmg_rowmajor_to_colmajor(m, n, t.data_ptr(), dt, work.data_ptr(), work.numel(),
+                                         _stream(t.device)), "jmg_rowmajor_to_colmajor")
+    return t.view(-1).view(n, m).t()
+
+
+def to_rowmajor_(t: torch.Tensor, work: torch.Tensor | None = None) -> torch.Tensor:
+    """The inverse of :func:`to_colmajor_`: a column-major m x n CUDA tensor
+    (stride (1, m), dense) becomes row-major in place; returns the row-major
+    (contiguous) view of the same storage."""
+    _need_cuda(t)
+    m, n = t.shape
+    if t.dim() != 2 or not (t.stride(0) == 1 and (t.stride(1) == m or n == 1)):
+        raise ValueError("to_rowmajor_: a dense column-major 2-D tensor is required")
+    dt = _dtype_code(t)
+    need = int(load().jmg_layout_workspace(n, m, dt))
+    if work is None:
+        work = torch.empty(max(need, 256), dtype=torch.uint8, device=t.device)
+    _chk(load().jmg_colmajor_to_rowmajor(m, n, t.data_ptr(), dt, work.data_ptr(), work.numel(),
+                                         _stream(t.device)), "jmg_colmajor_to_rowmajor")
+    return torch.as_strided(t, (m, n), (n, 1))
 
 
 def sym_grad(Bbar: torch.Tensor, X: torch.Tensor) -> torch.Tensor:

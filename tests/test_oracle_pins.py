@@ -297,10 +297,21 @@ def pin_bwd_err_rows_bit_identical(o):
     assert np.isnan(w1) and np.isnan(w2) and e1[0] == e2[0] and np.isnan(e2[1])
 
 
+def pin_layout_conversion(o):
+    # worked example by hand: the 2 x 3 matrix [[1, 2, 3], [4, 5, 6]] held
+    # row-major is [1 2 3 4 5 6]; column-major it is [1 4 2 5 3 6]
+    assert np.array_equal(o.rowmajor_to_colmajor(np.array([1., 2, 3, 4, 5, 6]), 2, 3),
+                          np.array([1., 4, 2, 5, 3, 6]))
+    # and NumPy's own column-major flattening of the same matrix
+    for m, n in [(1, 7), (7, 1), (5, 5), (6, 10), (13, 4)]:
+        M = np.random.default_rng(m * 31 + n).standard_normal((m, n))
+        assert np.array_equal(o.rowmajor_to_colmajor(M.reshape(-1), m, n), M.reshape(-1, order="F"))
+
+
 PINS = [pin_textbook, pin_integer_factor, pin_diag_closed_form, pin_ge_agrees, pin_ge_pivots,
         pin_known_solution, pin_scipy_cholesky, pin_potrs_residual, pin_dot2_exact,
         pin_bwd_err_formula, pin_not_spd, pin_logdet_library, pin_grad_fd, pin_grad_library,
-        pin_bwd_err_rows_bit_identical]
+        pin_bwd_err_rows_bit_identical, pin_layout_conversion]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=lambda p: p.__name__)
@@ -361,6 +372,8 @@ MUTANTS = {
     "rows_norm_no_abs": ("asum[ii] += fabs(a);", "asum[ii] += a;"),
     "rows_lower_only": ("const double a = sym_at(A, lda, i0 + ii, j);",
                         "const double a = j <= i0 + ii ? sym_at(A, lda, i0 + ii, j) : 0.0;"),
+    "layout_transposed": ("out[i + j * m] = in[i * n + j];", "out[i * n + j] = in[i + j * m];"),
+    "layout_wrong_stride": ("out[i + j * m] = in[i * n + j];", "out[i + j * n] = in[i * n + j];"),
     "rows_skip_tail": ("const int ib = n - i0 < ORACLE_ROWS ? n - i0 : ORACLE_ROWS;",
                        "const int ib = n - i0 < ORACLE_ROWS ? n - i0 - 1 : ORACLE_ROWS;"),
 }
