@@ -373,7 +373,8 @@ MUTANTS = {
     "rows_lower_only": ("const double a = sym_at(A, lda, i0 + ii, j);",
                         "const double a = j <= i0 + ii ? sym_at(A, lda, i0 + ii, j) : 0.0;"),
     "layout_transposed": ("out[i + j * m] = in[i * n + j];", "out[i * n + j] = in[i + j * m];"),
-    "layout_wrong_stride": ("out[i + j * m] = in[i * n + j];", "out[i + j * n] = in[i * n + j];"),
+    # planted mistakes stay inside the buffers: the mutant runs in this process
+    "layout_no_move": ("out[i + j * m] = in[i * n + j];", "out[i * n + j] = in[i * n + j];"),
     "rows_skip_tail": ("const int ib = n - i0 < ORACLE_ROWS ? n - i0 : ORACLE_ROWS;",
                        "const int ib = n - i0 < ORACLE_ROWS ? n - i0 - 1 : ORACLE_ROWS;"),
 }
