@@ -41,8 +41,8 @@ METRIC = ("posv TFLOP/s & time-to-solution at backward err ≤1e-13: mixed+IR vs
 
 # workload -> (n, nrhs, matrix kind, kappa or shift, precision, words)
 WORKLOADS = {
-    "c1": dict(n=1024, nrhs=1, kind="gram", param=1.0, prec="bf16", words=1,
-               desc="posv n=1024 nrhs=1, A = M M^T/n + I"),
+    "c1": dict(n=1024, nrhs=1, kind="gram", param=1.0, prec="fp32", words=1,
+               desc="posv n=1024 nrhs=1, A = M M^T/n + I (one-kernel FP32-factor path)"),
     "c2": dict(n=16384, nrhs=64, kind="qlam", param=1e6, prec="fp16", words=2,
                desc="posv n=16384 nrhs=64, A = Q diag(logspace[1,1e6]) Q^T, B = A X_true"),
     "c3": dict(n=32768, nrhs=16, kind="qlam", param=1e4, prec="fp16", words=2,
@@ -182,6 +182,29 @@ def make_inputs(w, device, seed=0, Q=None):
     B = inputs.rhs_from(A, Xt)
     torch.cuda.synchronize()
     return A, Xt, B
+
+
+def kappa_of_gram(A, shift, iters=20, seed=7):
+    """kappa of A = M M^T/n + shift*I, as far as it can be measured at this
+    size: lambda_max by power iteration (FP64 products, a lower bound that the
+    iteration approaches from below) and lambda_min >= shift (M M^T/n is
+    positive semidefinite; for square M its smallest eigenvalue is O(1/n^2),
+    so lambda_min is the shift up to that and the FP32 rounding of the
+    product).  A diagnostic outside the timed region."""
+    import torch
+
+    g = torch.Generator(device=A.device).manual_seed(seed)
+    v = torch.randn(A.shape[0], dtype=torch.float64, device=A.device, generator=g)
+    v /= v.norm()
+    lam = 0.0
+    for _ in range(iters):
+        w = A @ v
+        lam = float(torch.dot(v, w).item())
+        v = w / w.norm()
+    return {"lambda_max_power_iteration": lam, "power_iterations": iters,
+            "lambda_min_lower_bound": shift, "kappa": lam / shift,
+            "method": "lambda_max by power iteration (FP64 products); lambda_min = the "
+                      "shift up to O(1/n^2), since M M^T/n is positive semidefinite"}
 
 
 def host_f(t):
@@ -497,6 +520,9 @@ def run_main(args, w, rank, world):
     eta_or = certify(A_np, X_keep, B_keep) if rank == 0 else None
     eta64_or = certify(A_np, X64, B_keep) if (rank == 0 and X64 is not None) else None
     log("oracle certification: %.1f s" % (time.time() - t0))
+    kappa = kappa_of_gram(Acm, w["param"]) if w["kind"] in ("gram", "gram32") else (
+        {"kappa": w["param"], "method": "by construction (log-spaced spectrum)"}
+        if w["kind"] == "qlam" else None)
 
     value = replica_value(world, F, args.steps, t_mixed)
     peaks = load_peaks()
@@ -518,7 +544,7 @@ def run_main(args, w, rank, world):
                    "l2": "inputs larger than L2 (A = %.2f GB), no flush" % (n * n * 8 / 1e9)},
         "time_to_solution_ms": round(t_mixed * 1e3 / args.steps, 3),
         "bwd_err_oracle": eta_or, "bwd_err": eta, "bwd_err_componentwise": eta_cw,
-        "fwd_err": fwd,
+        "fwd_err": fwd, "kappa": kappa,
         "iters": [si.iters for si in infos],
         "refine_used": ["ir", "pcg", "auto"][infos[-1].refine_used] if infos[-1].refine_used >= 0 else None,
         "shift": infos[-1].shift, "factor_tries": infos[-1].factor_tries,
@@ -553,7 +579,10 @@ def run_main(args, w, rank, world):
 # capture, as a multiple of the algorithmic bytes at the captured size; the
 # kernel reads each byte of L once, so its traffic scales with the algorithmic
 # bytes.  None where the kernel changed since the capture.
-TRAFFIC_RATIO = {"solve": None, "residual_product": None}
+# From the full capture of both kernels at n = 8192, nrhs = 32 (FP8 posv):
+# residual product 1.0855 GB read+written for 1.0737 GB of slices, solve
+# 141.2 MB for 136.3 MB.
+TRAFFIC_RATIO = {"solve": 1.036, "residual_product": 1.011}
 
 
 def traffic_per_launch(kind, n, nrhs):
@@ -606,9 +635,16 @@ def run_extras(args, which):
             w = WORKLOADS[name]
             A, Xt, B = make_inputs(w, dev)
             A_np = host_f(A)
+            small = w["n"] <= 2048
             d, X = _one_config(jmg, torch, dev, stream, A, Xt, B, w["prec"], w["words"],
-                               steps=3, warmup=1)
+                               steps=10 if small else 3, warmup=3 if small else 1)
             d["bwd_err_oracle"] = certify(A_np, X, B)
+            if w["prec"] == "fp32":  # the tensor-core path on the same system, for context
+                d2, X2 = _one_config(jmg, torch, dev, stream, A, Xt, B, "bf16", 1, steps=5,
+                                     warmup=2)
+                d2["bwd_err_oracle"] = certify(A_np, X2, B)
+                d["tensor_core_path_bf16"] = d2
+                del X2
             f64_ms, X64 = _fp64_posv(jmg, A, B, stream, 3, warmup=1)
             t64 = statistics.mean(f64_ms)
             out[name] = {"workload": w["desc"], "n": w["n"], "nrhs": w["nrhs"], "mixed": d,

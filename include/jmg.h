@@ -78,7 +78,9 @@ typedef struct {
   double tol;       /* target normwise backward error of posv (mixed modes)         */
   int maxit;        /* maximum refinement iterations (IR steps + PCG steps)         */
   int refine;       /* jmg_refine                                                   */
-  int shift_retry;  /* low-precision breakdown: retry with a diagonal shift (0/1)   */
+  int shift_retry;  /* low-precision breakdown: retry with a diagonal shift (0/1): */
+                    /* u_f max|a_ii| / 4, then x4 per retry (u_f: the factor's unit */
+                    /* roundoff).  The FP8 factor always starts at that first shift */
   int timing;       /* 1: time the FP64 residual kernel with CUDA events (stats)    */
   int reuse_factor; /* mixed posv only: 1 = skip the factorisation and refine with  */
                     /* the factor that an earlier jmg_posv call with the same A, n  */
