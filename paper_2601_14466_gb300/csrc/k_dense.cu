@@ -37,11 +37,12 @@ int ensure_smem_raw(const void* func, int bytes) {
 //
 //  1. the 32 x 32 diagonal sub-block is factored in FP64 whatever the storage
 //     type T (double for the plain path, float for the FP32 working matrix of
-//     the mixed path).  Its 528 lower elements live in registers, three per
-//     thread; step j applies a_rc -= a_rj * a_cj / a_jj (= l_rj * l_cj) to
-//     every element with c > j, reading column j from a shared buffer that the
-//     owners of column j filled after their last update, so each column costs
-//     one barrier.  The owner of a_jj forms 1 / a_jj, the only operation on
+//     the mixed path).  Its 528 lower elements sit in shared memory as FP64;
+//     step j applies a_rc -= a_rj * a_cj / a_jj (= l_rj * l_cj) to every
+//     element with c > j, handing the trailing triangle's elements (a range of
+//     the packed column-major order) to consecutive threads so that FP64 work
+//     is issued by full warps only; each column costs one barrier.  The owner
+//     of a_(j+1)(j+1) forms 1 / a_(j+1)(j+1) in step j, the only operation on
 //     the serial chain besides the updates (exact for the plain path; an FP32
 //     seed plus one step of Newton's method for the mixed path, whose output is
 //     rounded to FP32 anyway); sqrt(a_jj) and its reciprocal follow after the
@@ -63,7 +64,6 @@ constexpr int BS = 32;                   // FP64 sub-block
 constexpr int TH = 256;
 constexpr int LD = KB + 4;               // shared leading dimension: 16-byte aligned columns
 constexpr int NEL = BS * (BS + 1) / 2;   // lower elements of a sub-block
-constexpr int SLOTS = (NEL + TH - 1) / TH;
 
 // 1 / d for the updates of step j (exact division for the plain path; for the
 // mixed path an FP32 seed and one step of Newton's method for 1/d, about 44
@@ -107,7 +107,6 @@ JMG_DEV void potrf_diag_body(T* __restrict__ A, int lda, int kb, int koff,
   using namespace pdiag;
   extern __shared__ __align__(16) unsigned char sm_diag[];
   T* sa = reinterpret_cast<T*>(sm_diag);  // kb columns, LD apart: sa[c * LD + r] = a_rc
-  __shared__ double col[2][BS];           // column j of the sub-block (double-buffered)
   __shared__ double s_l[BS], s_il[BS], s_w[BS];
   __shared__ T s_rinv[BS];
   __shared__ int fail;
@@ -128,36 +127,31 @@ JMG_DEV void potrf_diag_body(T* __restrict__ A, int lda, int kb, int koff,
       if (idx < kb * kb) sa[(idx / kb) * LD + idx % kb] = v[q];
     }
   }
-  // this thread's elements of a sub-block (packed column-major lower order)
-  int er[SLOTS], ec[SLOTS];
-#pragma unroll
-  for (int q = 0; q < SLOTS; ++q) {
-    int e = t + TH * q, c = 0;
-    if (e < NEL) {
-      while (e >= BS - c) e -= BS - c++;
-      er[q] = c + e;
-      ec[q] = c;
-    } else {
-      er[q] = ec[q] = -1;
-    }
+  // packed column-major lower order of a sub-block: element e <-> (row, column)
+  __shared__ unsigned short s_rc[NEL];
+  __shared__ double s64[BS * (BS + 1)];  // the FP64 sub-block: s64[c * (BS+1) + r]
+  for (int e = t; e < NEL; e += TH) {
+    int r = e, c = 0;
+    while (r >= BS - c) r -= BS - c++;
+    s_rc[e] = (unsigned short)((c << 8) | (c + r));
   }
   if (t == 0) fail = 0;
   __syncthreads();
 
   for (int p = 0; p < kb; p += BS) {
     const int bs = min(BS, kb - p);
-    // ---- 1. FP64 factor of the sub-block
-    double a[SLOTS];
-    int cc[SLOTS];  // column of the element, -1 when it is not in the sub-block
-#pragma unroll
-    for (int q = 0; q < SLOTS; ++q) {
-      cc[q] = (ec[q] >= 0 && er[q] < bs) ? ec[q] : -1;
-      a[q] = cc[q] >= 0 ? (double)sa[(p + cc[q]) * LD + p + er[q]] : 0.0;
-      if (cc[q] == 0) {
-        col[0][er[q]] = a[q];
-        if (er[q] == 0) pivot(0, a[q], kExact, s_w, &fail, p);
-      }
+    // ---- 1. FP64 factor of the sub-block.  Step j updates every element
+    // (r, c), c > j, of the trailing triangle: a_rc -= a_rj (a_cj w_j),
+    // w_j = 1/a_jj.  The elements of the trailing triangle are the packed
+    // indices from the start of column j+1 on, handed to consecutive threads,
+    // so every warp that issues FP64 work has all its lanes busy (a warp-wide
+    // FP64 instruction costs the same with one lane or 32).
+    for (int e = t; e < NEL; e += TH) {
+      const int rc = s_rc[e], c = rc >> 8, r = rc & 255;
+      if (r < bs) s64[c * (BS + 1) + r] = (double)sa[(p + c) * LD + p + r];
     }
+    __syncthreads();
+    if (t == 0) pivot(0, s64[0], kExact, s_w, &fail, p);
     __syncthreads();
     int jdone = bs;  // columns of the sub-block that are final
     for (int j = 0; j < bs; ++j) {
@@ -166,44 +160,39 @@ JMG_DEV void potrf_diag_body(T* __restrict__ A, int lda, int kb, int koff,
         break;
       }
       const double w = s_w[j];
-      const double* cj = col[j & 1];
-      double* cn = col[(j + 1) & 1];
-#pragma unroll
-      for (int q = 0; q < SLOTS; ++q) {
-        if (cc[q] > j) {
-          a[q] = fma(-cj[er[q]], cj[cc[q]] * w, a[q]);
-          if (cc[q] == j + 1) {
-            cn[er[q]] = a[q];
-            if (er[q] == j + 1) pivot(j + 1, a[q], kExact, s_w, &fail, p + j + 1);
-          }
-        }
+      const double* cj = &s64[j * (BS + 1)];
+      // first packed index of column j+1: sum of the column lengths before it
+      const int e0 = (j + 1) * BS - j * (j + 1) / 2;
+      for (int e = e0 + t; e < NEL; e += TH) {
+        const int rc = s_rc[e], c = rc >> 8, r = rc & 255;
+        if (r >= bs) continue;
+        const double v = fma(-cj[r], cj[c] * w, s64[c * (BS + 1) + r]);
+        s64[c * (BS + 1) + r] = v;
+        if (r == j + 1 && c == j + 1) pivot(j + 1, v, kExact, s_w, &fail, p + j + 1);
       }
       __syncthreads();
     }
     // L of the sub-block: l_cc = sqrt(a_cc), l_rc = a_rc / l_cc
-#pragma unroll
-    for (int q = 0; q < SLOTS; ++q) {
-      const int c = cc[q];
-      if (c >= 0 && c < jdone && er[q] == c) {
-        double l, il;
-        if (kExact || a[q] < 1e-30) {
-          l = sqrt(a[q]);
-          il = 1.0 / l;
-        } else {
-          const double y0 = (double)rsqrtf((float)a[q]);
-          il = y0 * fma(-0.5 * a[q], y0 * y0, 1.5);  // one Newton step for d^{-1/2}
-          l = a[q] * il;
-        }
-        s_l[c] = l;
-        s_il[c] = il;
+    if (t < jdone) {
+      const int c = t;
+      const double a = s64[c * (BS + 1) + c];
+      double l, il;
+      if (kExact || a < 1e-30) {
+        l = sqrt(a);
+        il = 1.0 / l;
+      } else {
+        const double y0 = (double)rsqrtf((float)a);
+        il = y0 * fma(-0.5 * a, y0 * y0, 1.5);  // one Newton step for d^{-1/2}
+        l = a * il;
       }
+      s_l[c] = l;
+      s_il[c] = il;
     }
     __syncthreads();
-#pragma unroll
-    for (int q = 0; q < SLOTS; ++q) {
-      const int c = cc[q], r = er[q];
-      if (c >= 0 && c < jdone) {
-        const T v = (T)(r == c ? s_l[c] : a[q] * s_il[c]);
+    for (int e = t; e < NEL; e += TH) {
+      const int rc = s_rc[e], c = rc >> 8, r = rc & 255;
+      if (r < bs && c < jdone) {
+        const T v = (T)(r == c ? s_l[c] : s64[c * (BS + 1) + r] * s_il[c]);
         sa[(p + c) * LD + p + r] = v;
         A[(size_t)(p + c) * lda + p + r] = v;
         if (r == c) s_rinv[c] = kExact ? (T)s_il[c] : (T)__frcp_rn((float)v);

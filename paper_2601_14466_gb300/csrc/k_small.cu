@@ -353,9 +353,9 @@ JMG_DEV void acc_to_S(float* S, const float (&acc)[4][4], float scale) {
 
 // Cholesky of the 64 x 64 tile S (LDS, lower) in FP32, in place, over four
 // 16-wide panels: (a) the 16 x 16 diagonal block by one warp in registers
-// (lane r holds row r; the right-looking update shares the scaled column by
-// shuffles), (b) the rows below it by substitution, one thread per row,
-// (c) the rank-16 update of the trailing lower triangle.  Returns 0 or the
+// (lane r holds row r; the unscaled right-looking update shares each column
+// by shuffles), (b) the rows below it by substitution, one thread per row,
+// (c) the rank-16 update of the trailing lower triangle in 4 x 4 tiles.  Returns 0 or the
 // 1-based index of the first pivot that is not > 0 and lies within the valid
 // order `rows` (the rest of the tile is the identity); every thread returns
 // the same value.
@@ -368,20 +368,31 @@ JMG_DEV int potf2_64(float* S, int rows, float* rinv, int* s_bc) {
 #pragma unroll
       for (int k = 0; k < 16; ++k) a[k] = S[(c0 + k) * LDS + c0 + r];
       int fail = 0;
+      // unscaled right-looking: a_rm -= a_rk a_mk / d_k; the column's values
+      // are shuffled before the pivot is known, so the chain per step is only
+      // shuffle, reciprocal, multiply, fma
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
+        float lm[16];
+#pragma unroll
+        for (int m = 1; m < 16; ++m)
+          if (m > k) lm[m] = __shfl_sync(0xffffffffu, a[k], m);
         float d = __shfl_sync(0xffffffffu, a[k], k);
         if (!(d > 0.0f) && !fail) fail = c0 + k + 1;
         if (fail) d = 1.0f;  // keep going on harmless numbers; the tile is dropped
-        const float il = rsqrtf(d), l = d * il;
-        a[k] = r == k ? l : (r > k ? a[k] * il : a[k]);
+        float rd;  // 1/d to within an ulp (an FP32 preconditioner; IEEE division would sit on the chain)
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rd) : "f"(d));
+        const float akw = a[k] * rd;
 #pragma unroll
-        for (int m = 1; m < 16; ++m) {  // constant trip count: a[] stays in registers
-          if (m > k) {
-            const float lm = __shfl_sync(0xffffffffu, a[k], m);
-            a[m] = r >= m ? fmaf(-a[k], lm, a[m]) : a[m];
-          }
-        }
+        for (int m = 1; m < 16; ++m)  // constant trip count: a[] stays in registers
+          if (m > k) a[m] = r >= m ? fmaf(-akw, lm[m], a[m]) : a[m];
+      }
+      // l_kk = sqrt(d_k), l_rk = a_rk / sqrt(d_k) (d_k: lane k's a[k])
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const float dk = __shfl_sync(0xffffffffu, a[k], k);
+        const float il = rsqrtf(fail ? 1.0f : dk);
+        a[k] = r > k ? a[k] * il : (r == k ? dk * il : a[k]);
         if (lane == k) rinv[c0 + k] = il;
       }
       if (lane < 16 && !fail) {
@@ -412,13 +423,38 @@ JMG_DEV int potf2_64(float* S, int rows, float* rinv, int* s_bc) {
       for (int k = 0; k < 16; ++k) S[(c0 + k) * LDS + R] = x[k];
     }
     __syncthreads();
-    for (int e = t; e < m * m; e += TH) {
-      const int r = c0 + 16 + e % m, c = c0 + 16 + e / m;
-      if (r < c) continue;
-      float v = S[c * LDS + r];
+    // rank-16 update of the trailing lower triangle, one 4 x 4 tile per thread
+    const int nt4 = m / 4;
+    if (t < nt4 * (nt4 + 1) / 2) {
+      int I = 0, J = t;  // tile (I, J), J <= I, numbered row by row
+      while (J > I) {
+        J -= I + 1;
+        ++I;
+      }
+      const int r0 = c0 + 16 + 4 * I, q0 = c0 + 16 + 4 * J;
+      float acc[4][4];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) v = fmaf(-S[(c0 + k) * LDS + r], S[(c0 + k) * LDS + c], v);
-      S[c * LDS + r] = v;
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        float xr[4], xc[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          xr[i] = S[(c0 + k) * LDS + r0 + i];
+          xc[i] = S[(c0 + k) * LDS + q0 + i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xr[i], xc[j], acc[i][j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (r0 + i >= q0 + j) S[(q0 + j) * LDS + r0 + i] -= acc[i][j];
     }
     __syncthreads();
   }
