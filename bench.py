@@ -620,6 +620,37 @@ def _one_config(jmg, torch, dev, stream, A, Xt, B, prec, words, steps=1, warmup=
     return d, X
 
 
+def _c_abi_small_ms(jmg, torch, A, B, stream, steps=20, warmup=5):
+    """The one-kernel path timed through the C ABI itself (jmg_posv with
+    pre-made pointers, options and workspace), without the Python binding's
+    per-call tensor set-up: the median of `steps` event-timed calls."""
+    import ctypes
+
+    n, nrhs = B.shape
+    o = jmg.default_options(prec="fp32")
+    work = jmg.workspace(jmg.OP_POSV, n, nrhs, o, A.device)
+    lib = jmg.load()
+    X = jmg.colmajor_copy(B)
+    info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    st = jmg.Stats()
+    args = (n, nrhs, A.data_ptr(), n, X.data_ptr(), n, jmg.JMG_F64, info.data_ptr(),
+            ctypes.byref(o), ctypes.byref(st), work.data_ptr(), work.numel(),
+            ctypes.c_void_p(stream.cuda_stream))
+    ms = []
+    for k in range(warmup + steps):
+        X.copy_(B)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = lib.jmg_posv(*args)
+        e1.record(stream)
+        e1.synchronize()
+        if rc != 0:
+            return None
+        if k >= warmup:
+            ms.append(e0.elapsed_time(e1))
+    return round(statistics.median(ms), 4)
+
+
 def run_extras(args, which):
     import numpy as np
     import torch
@@ -639,6 +670,8 @@ def run_extras(args, which):
             d, X = _one_config(jmg, torch, dev, stream, A, Xt, B, w["prec"], w["words"],
                                steps=10 if small else 3, warmup=3 if small else 1)
             d["bwd_err_oracle"] = certify(A_np, X, B)
+            if w["prec"] == "fp32":
+                d["c_abi_ms"] = _c_abi_small_ms(jmg, torch, A, B, stream)
             if w["prec"] == "fp32":  # the tensor-core path on the same system, for context
                 d2, X2 = _one_config(jmg, torch, dev, stream, A, Xt, B, "bf16", 1, steps=5,
                                      warmup=2)

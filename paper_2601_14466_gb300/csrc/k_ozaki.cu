@@ -26,8 +26,10 @@
 // 64-wide K block, then 8 A-slice tiles through a 6-stage ring), warp 1 issues
 // the MMAs (M = 128, K = 16, N = up to 256: consecutive X slices of one A
 // slice in one instruction), warps 2-17 drain
-// TMEM (up to four per TMEM lane quarter, 16 columns each).  All waits are
-// bounded.
+// TMEM (up to four per TMEM lane quarter, 16 columns each).  With 32 or fewer
+// right-hand sides per tile the eight accumulators fit twice in TMEM and
+// alternate by window, so the MMAs of a window overlap the drain of the last
+// one.  All waits are bounded.
 #include <algorithm>
 
 #include "kernels.h"
@@ -220,7 +222,10 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
   using namespace tc;
   constexpr int X_TILE = N * BK * 2;  // one slice: N rows x 128 bytes
   constexpr int X_BUF = S * X_TILE;
-  constexpr uint32_t TCOLS = (8 * N < 32) ? 32 : 8 * N;
+  // two accumulator sets where TMEM holds them (N <= 32): the MMAs of window
+  // w+1 run while the epilogue drains window w
+  constexpr int NBUF = (16 * N <= 512) ? 2 : 1;
+  constexpr uint32_t TCOLS = (NBUF * 8 * N < 32) ? 32 : NBUF * 8 * N;
   extern __shared__ __align__(1024) unsigned char sm_raw_oz[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(sm_raw_oz) + 1023) & ~uintptr_t(1023));
@@ -231,9 +236,9 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
   uint64_t* xempty = bars + 2;      // 2
   uint64_t* afull = bars + 4;       // ASTAGES
   uint64_t* aempty = afull + ASTAGES;
-  uint64_t* accf = aempty + ASTAGES;
-  uint64_t* acce = accf + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 1);
+  uint64_t* accf = aempty + ASTAGES;  // NBUF
+  uint64_t* acce = accf + NBUF;       // NBUF
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + NBUF);
   __shared__ int s_fail;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -254,8 +259,10 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
       mbar_init(&afull[i], 1);
       mbar_init(&aempty[i], 1);
     }
-    mbar_init(accf, 1);
-    mbar_init(acce, N * 4 / 16);
+    for (int i = 0; i < NBUF; ++i) {
+      mbar_init(&accf[i], 1);
+      mbar_init(&acce[i], N * 4 / 16);
+    }
     fence_mbar_init();
     prefetch_tmap(&tmA);
     prefetch_tmap(&tmX);
@@ -308,11 +315,14 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
       long long g = 0;
       bool ok = true;
       for (int w = w0; w < w1 && ok; ++w) {
-        if (w > w0 && !mbar_wait(acce, (uint32_t)((w - w0 - 1) & 1), wait_ns)) {
+        const int use = w - w0, bw = use % NBUF;  // accumulator set of this window
+        if (use >= NBUF &&
+            !mbar_wait(&acce[bw], (uint32_t)((use / NBUF - 1) & 1), wait_ns)) {
           ok = false;
           break;
         }
         tc_fence_after();
+        const uint32_t tacc = tmem + (uint32_t)(bw * 8 * N);
         const int kbw0 = max(kb0, w * WIN), kbw1 = min(kb1, (w + 1) * WIN);
         for (int kb = kbw0; kb < kbw1 && ok; ++kb) {
           const int u = kb - kb0, xs = u & 1;
@@ -337,7 +347,7 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
             for (int b0 = 0; b0 < S - a; b0 += GMAX) {
               const int cnt = min(GMAX, S - a - b0);
               const uint32_t idesc_g = idesc_f16(BM, N * cnt, 1);
-              const uint32_t dacc = tmem + (uint32_t)((a + b0) * N);
+              const uint32_t dacc = tacc + (uint32_t)((a + b0) * N);
 #pragma unroll
               for (int kk = 0; kk < 4; ++kk) {
                 const bool first = (kb == kbw0) && (a == 0) && (kk == 0);
@@ -349,7 +359,7 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
           }
           tc_commit(&xempty[xs]);
         }
-        tc_commit(accf);
+        tc_commit(&accf[bw]);
       }
       if (!ok) atomicExch(&s_fail, 1);
     }
@@ -372,18 +382,21 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
       for (int c = 0; c < CW; ++c) hs[c] = ls[c] = 0ull;
       bool ok = true;
       for (int w = w0; w < w1; ++w) {
-        if (!mbar_wait(accf, (uint32_t)((w - w0) & 1), wait_ns) || ld_shared_volatile(&s_fail)) {
+        const int use = w - w0, bw = use % NBUF;
+        if (!mbar_wait(&accf[bw], (uint32_t)((use / NBUF) & 1), wait_ns) ||
+            ld_shared_volatile(&s_fail)) {
           ok = false;
           break;
         }
         tc_fence_after();
+        const uint32_t tacc = tmem + (uint32_t)(bw * 8 * N);
 #pragma unroll
         for (int d = 0; d < S; ++d) {
           const long long sc = 1ll << (d <= 3 ? 21 - 7 * d : 49 - 7 * d);
 #pragma unroll
           for (int c0 = 0; c0 < CW; c0 += 16) {
             uint32_t v[16];
-            tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * N + ch + c0), v);
+            tmem_ld16(tacc + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * N + ch + c0), v);
             tmem_ld_wait();
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
@@ -397,7 +410,7 @@ __global__ void __launch_bounds__(oz::THREADS, 1)
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(acce);
+        if (lane == 0) mbar_arrive(&acce[bw]);
       }
       if (ok) {
         const int row = rt * BM + q * 32 + lane;

@@ -270,8 +270,9 @@ def _solve_info(stats: Stats) -> SolveInfo:
                      stats.h2d_bytes, stats.d2h_bytes)
 
 
-def _options(prec, words, nb, tol, maxit, refine, shift_retry, timing, reuse_factor, resid):
-    return default_options(nb=nb, prec=prec, words=words, tol=tol, maxit=maxit, refine=refine,
+def _options(prec, words, nb, tol, maxit, refine, shift_retry, timing, reuse_factor, resid,
+             NB=None):
+    return default_options(nb=nb, NB=NB, prec=prec, words=words, tol=tol, maxit=maxit, refine=refine,
                            shift_retry=int(shift_retry), timing=int(timing),
                            reuse_factor=int(reuse_factor),
                            resid={"auto": 0, "fp64": 1, "split": 2}[resid])
@@ -280,7 +281,8 @@ def _options(prec, words, nb, tol, maxit, refine, shift_retry, timing, reuse_fac
 def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1, nb: int = 128,
          tol: float = 1e-13, maxit: int = 300, refine: str = "auto", shift_retry: bool = True,
          overwrite_a: bool = False, work: torch.Tensor | None = None, check: bool = True,
-         timing: bool = False, reuse_factor: bool = False, resid: str = "auto"):
+         timing: bool = False, reuse_factor: bool = False, resid: str = "auto",
+         NB: int | None = None):
     """Solve A X = B for SPD A (lower triangle of the column-major A read).
 
     prec "fp64": potrf + potrs in FP64 (A is overwritten with L only when
@@ -301,11 +303,14 @@ def posv(A: torch.Tensor, B: torch.Tensor, *, prec: str = "fp64", words: int = 1
         B = B.reshape(-1, 1)
     n, nrhs = A.shape[0], B.shape[1]
     X = colmajor_copy(B)
-    o = _options(prec, words, nb, tol, maxit, refine, shift_retry, timing, reuse_factor, resid)
+    o = _options(prec, words, nb, tol, maxit, refine, shift_retry, timing, reuse_factor, resid,
+                 NB)
     Aw = A if (overwrite_a or o.prec != 0) else colmajor_copy(A)
     pa, lda = _colmajor(Aw, "A")
     px, ldx = _colmajor(X, "B")
-    info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    # the plain path reports through info (zeroed here); the mixed paths write it
+    # themselves and report through the status and stats
+    info = (torch.zeros if o.prec == 0 else torch.empty)(1, dtype=torch.int32, device=A.device)
     stats = Stats()
     if work is None:
         work = workspace(OP_POSV, n, nrhs, o, A.device)
