@@ -466,7 +466,6 @@ __global__ void __launch_bounds__(ptrsm::TH, 1) k_trsm_rows(float* __restrict__ 
   float(*Xt)[LDX] = reinterpret_cast<float(*)[LDX]>(sm_trows + KB * KB);  // KB x RB (column-major tile)
   float* rinv = sm_trows + KB * KB + KB * LDX;
   const int t = threadIdx.x;
-  const int r0 = blockIdx.x * RB;
   for (int base = 0; base < KB * KB; base += TH * 16) {  // 16 independent loads per thread
     float v[16];
 #pragma unroll
@@ -481,6 +480,12 @@ __global__ void __launch_bounds__(ptrsm::TH, 1) k_trsm_rows(float* __restrict__ 
       if (idx < KB * KB) Lt[idx / KB][idx % KB] = v[q];
     }
   }
+  __syncthreads();  // Lt complete before its diagonal is read
+  if (t < KB) rinv[t] = 1.0f / Lt[t][t];
+  const int rl = t / 4, g = t % 4, lane = t % 32;
+  // L_kk stays in shared memory; the CTA takes 64-row tiles in turn
+  for (int r0 = blockIdx.x * RB; r0 < m; r0 += gridDim.x * RB) {
+  __syncthreads();  // Lt, rinv ready; the previous tile's Xt is stored
   for (int base = 0; base < KB * RB; base += TH * 16) {
     float v[16];
 #pragma unroll
@@ -496,9 +501,6 @@ __global__ void __launch_bounds__(ptrsm::TH, 1) k_trsm_rows(float* __restrict__ 
     }
   }
   __syncthreads();
-  if (t < KB) rinv[t] = 1.0f / Lt[t][t];
-  __syncthreads();
-  const int rl = t / 4, g = t % 4, lane = t % 32;
 #pragma unroll 1
   for (int J = 0; J < KB / 32; ++J) {
     const int j0 = J * 32, cb = j0 + 8 * g;  // this thread's 8 columns
@@ -542,6 +544,7 @@ __global__ void __launch_bounds__(ptrsm::TH, 1) k_trsm_rows(float* __restrict__ 
     const int r = idx % RB, c = idx / RB;
     if (r0 + r < m) A21[(size_t)c * lda + r0 + r] = Xt[c][r];
   }
+  }
 }
 
 int launch_trsm(float* A21, int lda, int m, int kb, const float* Lkk, const int* info,
@@ -551,7 +554,12 @@ int launch_trsm(float* A21, int lda, int m, int kb, const float* Lkk, const int*
     auto k = (kb == 128) ? k_trsm_rows<128> : k_trsm_rows<64>;
     const size_t smem = sizeof(float) * ((size_t)kb * kb + (size_t)kb * ptrsm::LDX + kb);
     JMG_TRY(ensure_smem(k, (int)smem));
-    k<<<cdiv(m, ptrsm::RB), ptrsm::TH, smem, s>>>(A21, lda, m, Lkk, info);
+    int dev = 0, nsm = 152, per_sm = 1;
+    JMG_CUDA(cudaGetDevice(&dev));
+    JMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    JMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, ptrsm::TH, smem));
+    const int grid = std::max(1, std::min(cdiv(m, ptrsm::RB), std::max(per_sm, 1) * nsm));
+    k<<<grid, ptrsm::TH, smem, s>>>(A21, lda, m, Lkk, info);
     return launched();
   }
   return trsm_impl<float, 64>(A21, lda, m, kb, Lkk, info, s);
@@ -1226,15 +1234,32 @@ namespace jmg {
 __global__ void __launch_bounds__(256) k_quant_fp8(int m, int kb, const float* __restrict__ L21,
                                                    int ldw, unsigned char* __restrict__ Q, int ldq,
                                                    signed char* __restrict__ ex) {
+  // the tile goes through shared memory (column c at c * 129): read along the
+  // columns of L21 (coalesced, 16 loads in flight per thread, amax on the way),
+  // written along the rows of Q (four codes per 32-bit store)
+  extern __shared__ float qtile[];
+  constexpr int LDT = 129;
   __shared__ float red[8];
   __shared__ int s_e;
   const int r0 = blockIdx.x * 128;
   const int rows = min(128, m - r0);
   const int t = threadIdx.x;
   float amax = 0.0f;
-  for (int idx = t; idx < rows * kb; idx += 256) {
-    const int i = idx % rows, c = idx / rows;
-    amax = fmaxf(amax, fabsf(L21[(size_t)c * ldw + r0 + i]));
+  for (int base = 0; base < 128 * kb; base += 256 * 16) {
+    float v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int idx = base + t + 256 * q, i = idx & 127, c = idx >> 7;
+      v[q] = (idx < 128 * kb && i < rows) ? L21[(size_t)c * ldw + r0 + i] : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int idx = base + t + 256 * q;
+      if (idx < 128 * kb) {
+        qtile[(idx >> 7) * LDT + (idx & 127)] = v[q];
+        amax = fmaxf(amax, fabsf(v[q]));
+      }
+    }
   }
   for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   if ((t & 31) == 0) red[t / 32] = amax;
@@ -1253,19 +1278,27 @@ __global__ void __launch_bounds__(256) k_quant_fp8(int m, int kb, const float* _
     ex[blockIdx.x] = (signed char)e;
   }
   __syncthreads();
-  const int e = s_e;
-  // write row-major: consecutive threads take consecutive columns of a row
-  for (int idx = t; idx < rows * kb; idx += 256) {
-    const int c = idx % kb, i = idx / kb;
-    const float v = ldexpf(L21[(size_t)c * ldw + r0 + i], e);
-    Q[(size_t)(r0 + i) * ldq + c] = (unsigned char)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+  const int e = s_e, kq = kb / 4;
+  for (int idx = t; idx < rows * kq; idx += 256) {
+    const int i = idx / kq, c = (idx % kq) * 4;
+    unsigned int w = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float v = ldexpf(qtile[(c + u) * LDT + i], e);
+      w |= (unsigned int)(unsigned char)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3)
+           << (8 * u);
+    }
+    *reinterpret_cast<unsigned int*>(Q + (size_t)(r0 + i) * ldq + c) = w;
   }
 }
 
 int launch_quant_fp8(int m, int kb, const float* L21, int ldw, void* Q, int ldq, signed char* e,
                      cudaStream_t s) {
   if (m <= 0) return JMG_OK;
-  k_quant_fp8<<<cdiv(m, 128), 256, 0, s>>>(m, kb, L21, ldw, (unsigned char*)Q, ldq, e);
+  if (kb % 4 || ldq % 4 || (reinterpret_cast<uintptr_t>(Q) & 3)) return JMG_ERR_ALIGN;
+  const int smem = (int)sizeof(float) * kb * 129;
+  JMG_TRY(ensure_smem(k_quant_fp8, smem));
+  k_quant_fp8<<<cdiv(m, 128), 256, smem, s>>>(m, kb, L21, ldw, (unsigned char*)Q, ldq, e);
   return launched();
 }
 
