@@ -354,7 +354,8 @@ JMG_DEV void acc_to_S(float* S, const float (&acc)[4][4], float scale) {
 // Cholesky of the 64 x 64 tile S (LDS, lower) in FP32, in place, over four
 // 16-wide panels: (a) the 16 x 16 diagonal block by one warp in registers
 // (lane r holds row r; the unscaled right-looking update shares each column
-// by shuffles), (b) the rows below it by substitution, one thread per row,
+// through shared memory), (b) the rows below it by substitution, one thread per
+// row,
 // (c) the rank-16 update of the trailing lower triangle in 4 x 4 tiles.  Returns 0 or the
 // 1-based index of the first pivot that is not > 0 and lies within the valid
 // order `rows` (the rest of the tile is the identity); every thread returns
@@ -363,42 +364,51 @@ JMG_DEV int potf2_64(float* S, int rows, float* rinv, int* s_bc) {
   const int t = threadIdx.x, lane = t & 31;
   for (int c0 = 0; c0 < NB; c0 += 16) {
     if (t < 32) {
-      const int r = lane & 15;
-      float a[16];
+      // lane (r, h) holds row r, columns 8h .. 8h+7 of the 16 x 16 block
+      const int r = lane & 15, h = lane >> 4;
+      float a[8];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) a[k] = S[(c0 + k) * LDS + c0 + r];
+      for (int j = 0; j < 8; ++j) a[j] = S[(c0 + 8 * h + j) * LDS + c0 + r];
       int fail = 0;
-      // unscaled right-looking: a_rm -= a_rk a_mk / d_k; the column's values
-      // are shuffled before the pivot is known, so the chain per step is only
-      // shuffle, reciprocal, multiply, fma
+      // unscaled right-looking: a_rm -= a_rk a_mk / d_k.  Each step the half
+      // holding column k puts it in shared memory (double-buffered by step);
+      // every lane reads the pivot, its own a_rk and the a_mk of its columns
+      // back as broadcasts (15 shuffles per step by one half-warp measured
+      // ~3x slower)
+      __shared__ float colb[2][16];
+      __shared__ float piv[16];
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
-        float lm[16];
-#pragma unroll
-        for (int m = 1; m < 16; ++m)
-          if (m > k) lm[m] = __shfl_sync(0xffffffffu, a[k], m);
-        float d = __shfl_sync(0xffffffffu, a[k], k);
+        if (h == (k >> 3)) colb[k & 1][r] = a[k & 7];
+        __syncwarp();
+        float d = colb[k & 1][k];
+        if (lane == 0) piv[k] = d;
         if (!(d > 0.0f) && !fail) fail = c0 + k + 1;
         if (fail) d = 1.0f;  // keep going on harmless numbers; the tile is dropped
         float rd;  // 1/d to within an ulp (an FP32 preconditioner; IEEE division would sit on the chain)
         asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rd) : "f"(d));
-        const float akw = a[k] * rd;
+        const float akw = colb[k & 1][r] * rd;
 #pragma unroll
-        for (int m = 1; m < 16; ++m)  // constant trip count: a[] stays in registers
-          if (m > k) a[m] = r >= m ? fmaf(-akw, lm[m], a[m]) : a[m];
+        for (int j = 0; j < 8; ++j) {
+          const int m = 8 * h + j;
+          if (m > k && r >= m) a[j] = fmaf(-akw, colb[k & 1][m], a[j]);
+        }
       }
-      // l_kk = sqrt(d_k), l_rk = a_rk / sqrt(d_k) (d_k: lane k's a[k])
+      __syncwarp();
+      // l_kk = sqrt(d_k), l_rk = a_rk / sqrt(d_k)
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const float dk = __shfl_sync(0xffffffffu, a[k], k);
+      for (int j = 0; j < 8; ++j) {
+        const int k = 8 * h + j;
+        const float dk = piv[k];
         const float il = rsqrtf(fail ? 1.0f : dk);
-        a[k] = r > k ? a[k] * il : (r == k ? dk * il : a[k]);
-        if (lane == k) rinv[c0 + k] = il;
+        a[j] = r > k ? a[j] * il : (r == k ? dk * il : a[j]);
+        if (r == k) rinv[c0 + k] = il;
       }
-      if (lane < 16 && !fail) {
+      if (!fail) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const float v = a[k];
+        for (int j = 0; j < 8; ++j) {
+          const int k = 8 * h + j;
+          const float v = a[j];
           if (k <= r) S[(c0 + k) * LDS + c0 + r] = v;
         }
       }
