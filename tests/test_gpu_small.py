@@ -124,3 +124,19 @@ def test_small_posv_wait_runs_out():
         jmg.set_wait_limit_ns(old)
     assert si.status == JMG_ERR_TIMEOUT
     _solve_check(A, B, kappa=10.0)
+
+
+def test_small_posv_nan_rhs_stops():
+    # a NaN in B makes its residual NaN: the device-side rule stops at the first
+    # check (no refinement steps) and reports NOT_CONVERGED; the other columns
+    # are unaffected by the bad one only through the shared stopping decision
+    n = 300
+    A = inputs.gram_shift(n, 1.0, seed=51)
+    B = inputs.rhs_from(A, inputs.uniform(n, 2, seed=52))
+    B[7, 1] = float("nan")
+    Ad, _ = to_dev_colmajor(A)
+    Bd, _ = to_dev_colmajor(B)
+    X, si = jmg.posv(Ad, Bd, prec="fp32", check=False)
+    assert si.status == 4  # JMG_ERR_NOT_CONVERGED
+    assert si.iters == 0 and np.isnan(si.bwd_err)
+    assert np.isnan(host(X)[:, 1]).any()
