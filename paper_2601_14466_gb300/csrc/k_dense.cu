@@ -64,26 +64,35 @@ constexpr int BS = 32;                   // FP64 sub-block
 constexpr int TH = 256;
 constexpr int LD = KB + 4;               // shared leading dimension: 16-byte aligned columns
 constexpr int NEL = BS * (BS + 1) / 2;   // lower elements of a sub-block
+static_assert(TH == 256, "the FP64 step's warp roles and its named barrier (224 threads) assume 8 warps");
+
+// 1/d to about 44 bits for positive normal d with |log2 d| <= 100: the leading
+// bits of d as an FP32 number (exponent rebiased, mantissa truncated, with
+// integer operations that stay off the FP64 pipe, where a conversion costs as
+// much as an FMA), rcp.approx on it, the FP32 result widened the same way, and
+// one step of Newton's method for 1/d in FP64.
+JMG_DEV double rcp_seeded(double d) {
+  const int hi = __double2hiint(d);
+  const unsigned lo = (unsigned)__double2loint(d);
+  const int fb = ((((hi >> 20) & 0x7ff) - 896) << 23) | ((hi & 0xfffff) << 3) | (int)(lo >> 29);
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(__int_as_float(fb)));
+  const int yb = __float_as_int(y);
+  const double y0 =
+      __hiloint2double(((((yb >> 23) & 0xff) + 896) << 20) | ((yb & 0x7fffff) >> 3), (yb & 7) << 29);
+  return fma(y0, fma(-d, y0, 1.0), y0);
+}
 
 // 1 / d for the updates of step j (exact division for the plain path; for the
-// mixed path an FP32 seed and one step of Newton's method for 1/d, about 44
-// bits, whose result is rounded to FP32 anyway).  Only this reciprocal sits on
-// the serial chain of the steps; sqrt(d) is taken after the last step.
-JMG_DEV void pivot(int j, double d, bool exact, double* s_w, int* fail, int gj) {
-  if (!(d > 0.0)) {
-    *fail = gj + 1;
-    return;
-  }
-  double w;
-  if (exact || d < 1e-30) {  // (below the FP32 normal range the seed is useless)
-    w = 1.0 / d;
-  } else {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"((float)d));
-    const double y0 = (double)y;
-    w = fma(y0, fma(-d, y0, 1.0), y0);
-  }
-  s_w[j] = w;
+// mixed path the seeded Newton step above, whose result is rounded to FP32
+// anyway).  Only this reciprocal sits on the serial chain of the steps; sqrt(d)
+// is taken after the last step.  *bad is set when d is not positive (or NaN);
+// the result is then finite garbage or non-finite, never a trap.
+JMG_DEV double pivot_w(double d, bool exact, bool* bad) {
+  const int hi = __double2hiint(d), e = (hi >> 20) & 0x7ff;
+  if (!exact && hi >= 0 && e >= 1023 - 100 && e <= 1023 + 100) return rcp_seeded(d);
+  *bad = !(d > 0.0);
+  return 1.0 / d;
 }
 
 template <typename T>
@@ -107,12 +116,14 @@ JMG_DEV void potrf_diag_body(T* __restrict__ A, int lda, int kb, int koff,
   using namespace pdiag;
   extern __shared__ __align__(16) unsigned char sm_diag[];
   T* sa = reinterpret_cast<T*>(sm_diag);  // kb columns, LD apart: sa[c * LD + r] = a_rc
-  __shared__ double s_l[BS], s_il[BS], s_w[BS];
+  __shared__ double s_l[BS], s_il[BS], s_u[2][BS];
   __shared__ T s_rinv[BS];
   __shared__ int fail;
-  if (*(volatile int*)info != 0) return;  // an earlier block already failed
   constexpr bool kExact = sizeof(T) == 8;
   const int t = threadIdx.x;
+  if (t == 0) fail = *(volatile int*)info;  // one read, so every thread takes the same exit
+  __syncthreads();
+  if (fail != 0) return;  // an earlier block already failed
   for (int base = 0; base < kb * kb; base += TH * 16) {  // 16 independent loads per thread
     T v[16];
 #pragma unroll
@@ -135,43 +146,90 @@ JMG_DEV void potrf_diag_body(T* __restrict__ A, int lda, int kb, int koff,
     while (r >= BS - c) r -= BS - c++;
     s_rc[e] = (unsigned short)((c << 8) | (c + r));
   }
-  if (t == 0) fail = 0;
   __syncthreads();
 
   for (int p = 0; p < kb; p += BS) {
     const int bs = min(BS, kb - p);
     // ---- 1. FP64 factor of the sub-block.  Step j updates every element
-    // (r, c), c > j, of the trailing triangle: a_rc -= a_rj (a_cj w_j),
-    // w_j = 1/a_jj.  The elements of the trailing triangle are the packed
-    // indices from the start of column j+1 on, handed to consecutive threads,
-    // so every warp that issues FP64 work has all its lanes busy (a warp-wide
-    // FP64 instruction costs the same with one lane or 32).
+    // (r, c), c > j, of the trailing triangle: a_rc -= a_rj u_c with
+    // u_c = a_cj w_j, w_j = 1/a_jj.  A warp-wide FP64 instruction occupies its
+    // SM sub-partition's FP64 pipe for ~64 cycles whatever the active lanes,
+    // and the pivots form a serial chain, so the work is split by warp and
+    // the chain runs one column ahead of the rest:
+    //  * warp 0 (the chain) keeps column j and w_j in registers (one lane per
+    //    row); in step j it forms u, hands it to the trailing warps (named
+    //    barrier U), finishes column j+1 (its update by column j) and takes
+    //    pivot j+1 on every lane;
+    //  * warps 1-3 and 5-7 (trailing) take u_j and update column j+2 first,
+    //    release it (named barrier Y: the chain's input of step j+1), then
+    //    the columns j+3.. (packed indices on consecutive threads);
+    //  * warp 4, which shares warp 0's FP64 pipe, stays out.
+    // The last step has no work, so both sides run steps 0..bs-2.  Each
+    // barrier is passed the same number of times on both sides (U: bs-1,
+    // Y: bs-2), and every arrival waits, through the other barrier, for the
+    // other side to have passed the previous instance, so no instance can
+    // count an arrival meant for the next.  Nothing leaves the loop early: a
+    // pivot that is not positive is recorded (the first one wins) and the
+    // columns from it on are dropped after the loop.  u alternates between
+    // two buffers; the chain writes buffer j&1 only after passing Y of step
+    // j-1, i.e. after the trailing warps have finished step j-2.
     for (int e = t; e < NEL; e += TH) {
       const int rc = s_rc[e], c = rc >> 8, r = rc & 255;
       if (r < bs) s64[c * (BS + 1) + r] = (double)sa[(p + c) * LD + p + r];
     }
     __syncthreads();
-    if (t == 0) pivot(0, s64[0], kExact, s_w, &fail, p);
-    __syncthreads();
-    int jdone = bs;  // columns of the sub-block that are final
-    for (int j = 0; j < bs; ++j) {
-      if (fail) {
-        jdone = j;
-        break;
+    const int warp = t >> 5, lane = t & 31;
+    if (warp == 0) {
+      const bool row = lane < bs;
+      double colj = row ? s64[lane] : 0.0;  // column 0
+      bool bad = false;
+      double w = pivot_w(__shfl_sync(0xffffffffu, colj, 0), kExact, &bad);
+      int fj = bad ? 0 : -1;  // first failing column of the sub-block
+      for (int j = 0; j + 1 < bs; ++j) {
+        const bool own = row && lane > j;  // rows below the diagonal of column j
+        __syncwarp();
+        if (j > 0) asm volatile("bar.sync 2, 224;" ::: "memory");  // column j+1 done to j-1
+        double nxt = own ? s64[(j + 1) * (BS + 1) + lane] : 0.0;
+        const double u = own ? colj * w : 0.0;
+        if (own) s_u[j & 1][lane] = u;
+        __syncwarp();
+        asm volatile("bar.arrive 1, 224;" ::: "memory");
+        nxt = fma(-colj, __shfl_sync(0xffffffffu, u, j + 1), nxt);
+        if (own) s64[(j + 1) * (BS + 1) + lane] = nxt;
+        bad = false;
+        const double wn = pivot_w(__shfl_sync(0xffffffffu, nxt, j + 1), kExact, &bad);
+        if (bad && fj < 0) fj = j + 1;
+        colj = nxt;
+        w = wn;
       }
-      const double w = s_w[j];
-      const double* cj = &s64[j * (BS + 1)];
-      // first packed index of column j+1: sum of the column lengths before it
-      const int e0 = (j + 1) * BS - j * (j + 1) / 2;
-      for (int e = e0 + t; e < NEL; e += TH) {
-        const int rc = s_rc[e], c = rc >> 8, r = rc & 255;
-        if (r >= bs) continue;
-        const double v = fma(-cj[r], cj[c] * w, s64[c * (BS + 1) + r]);
-        s64[c * (BS + 1) + r] = v;
-        if (r == j + 1 && c == j + 1) pivot(j + 1, v, kExact, s_w, &fail, p + j + 1);
+      if (lane == 0 && fj >= 0) fail = p + fj + 1;
+    } else if (warp != 4) {
+      const int tq = warp < 4 ? t - 32 : t - 64;  // index among the trailing warps
+      for (int j = 0; j + 1 < bs; ++j) {
+        __syncwarp();
+        asm volatile("bar.sync 1, 224;" ::: "memory");  // u_j and column j in place
+        const double* cj = &s64[j * (BS + 1)];
+        const double* uj = s_u[j & 1];
+        if (j + 2 < bs) {
+          if (tq >= j + 2 && tq < bs) {
+            double* c2 = &s64[(j + 2) * (BS + 1)];
+            c2[tq] = fma(-cj[tq], uj[j + 2], c2[tq]);
+          }
+          __syncwarp();
+          asm volatile("bar.arrive 2, 224;" ::: "memory");
+        }
+        // first packed index of column j+3: sum of the column lengths before it
+        const int c3 = j + 3;
+        const int e3 = c3 >= BS ? NEL : c3 * BS - c3 * (c3 - 1) / 2;
+        for (int e = e3 + tq; e < NEL; e += TH - 64) {
+          const int rc = s_rc[e], c = rc >> 8, r = rc & 255;
+          if (r >= bs) continue;
+          s64[c * (BS + 1) + r] = fma(-cj[r], uj[c], s64[c * (BS + 1) + r]);
+        }
       }
-      __syncthreads();
     }
+    __syncthreads();
+    const int jdone = fail ? fail - 1 - p : bs;  // columns of the sub-block that are final
     // L of the sub-block: l_cc = sqrt(a_cc), l_rc = a_rc / l_cc
     if (t < jdone) {
       const int c = t;
@@ -198,7 +256,7 @@ JMG_DEV void potrf_diag_body(T* __restrict__ A, int lda, int kb, int koff,
         if (r == c) s_rinv[c] = kExact ? (T)s_il[c] : (T)__frcp_rn((float)v);
       }
     }
-    if (jdone < bs) break;  // (uniform: every thread read the same flag)
+    if (jdone < bs) break;  // (uniform: every thread read the same flag after the barrier)
     const int mr = kb - p - BS;
     if (mr <= 0) break;
     __syncthreads();
