@@ -137,11 +137,12 @@ class ClockSampler:
                 if len(p) < 9:
                     continue
                 try:
-                    sm.append(float(p[1]))
-                    smax.append(float(p[2]))
-                    power.append(float(p[3]))
+                    vals = float(p[1]), float(p[2]), float(p[3])
                 except ValueError:
                     continue
+                sm.append(vals[0])
+                smax.append(vals[1])
+                power.append(vals[2])
                 for nm, v in zip(names, p[5:9]):
                     if v.lower() == "active":
                         reasons.add(nm)
