@@ -136,6 +136,11 @@ class ClockSampler:
                 p = [x.strip() for x in line.split(",")]
                 if len(p) < 9:
                     continue
+                # a throttle reason counts even where a number is unreadable;
+                # the numbers of a sample count only if all three are readable
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
                 try:
                     vals = float(p[1]), float(p[2]), float(p[3])
                 except ValueError:
@@ -143,9 +148,6 @@ class ClockSampler:
                 sm.append(vals[0])
                 smax.append(vals[1])
                 power.append(vals[2])
-                for nm, v in zip(names, p[5:9]):
-                    if v.lower() == "active":
-                        reasons.add(nm)
             os.unlink(self.path)
         except Exception:
             pass

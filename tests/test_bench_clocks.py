@@ -73,9 +73,9 @@ def test_malformed_lines_are_skipped():
     rec = _stop_with(["", "0, [N/A], 2070, 100.0, 0x0, Not Active, Not Active, Not Active, Not Active",
                       "0, 1500, 2070, [N/A], 0x0, Active, Not Active, Not Active, Not Active",
                       "garbage", _line(2040, 2070, 700.0)])
-    assert rec["sm_mhz"] == 2040.0  # a line with any unreadable number counts for nothing
+    assert rec["sm_mhz"] == 2040.0  # numbers count only from lines where all are readable
     assert rec["samples"] == 1
-    assert rec["reasons"] == []
+    assert rec["reasons"] == ["hw_slowdown"]  # a throttle reason counts wherever it is read
 
 
 def test_no_sampler_says_so():
